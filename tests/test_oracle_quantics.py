@@ -1,0 +1,31 @@
+"""Pins of the scale-ordered codec (Sec. 2.4): bijection and bit positions."""
+import numpy as np
+
+from oracle import quantics as q
+
+
+def test_roundtrip():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 3):
+        N = 1 << n
+        a = rng.standard_normal((N, N, N))
+        t = q.encode(a)
+        assert t.shape == (2,) * (3 * n)
+        np.testing.assert_array_equal(q.decode(t), a)
+
+
+def test_bit_positions():
+    # a single 1 at (x, y, z) must appear at the site bits MSB-first, x-y-z interleaved
+    n = 3
+    N = 8
+    for (x, y, z) in [(5, 2, 7), (1, 0, 4), (7, 7, 0)]:
+        a = np.zeros((N, N, N))
+        a[x, y, z] = 1.0
+        idx = np.argwhere(q.encode(a) == 1.0)
+        assert len(idx) == 1
+        bits = idx[0]
+        for lev in range(n):
+            assert bits[3 * lev + 0] == (x >> (n - 1 - lev)) & 1
+            assert bits[3 * lev + 1] == (y >> (n - 1 - lev)) & 1
+            assert bits[3 * lev + 2] == (z >> (n - 1 - lev)) & 1
+        assert q.site_of(2, 1) == 5
