@@ -1,0 +1,337 @@
+"""Benchmark of the MPS lattice Boltzmann step on GB300.
+
+Default workload (the configuration the metric is quoted on): porous medium,
+128^3 D3Q19 BGK, tau = 0.7, seeded sphere pack (radius 10 cells, 35 % solid,
+periodic), mask compressed as an MPS (chi_mask = 64), body force 1e-5 along x
+standing in for the pressure drive, chi_max = 64, FP32 storage and contractions
+with FP64 singular-value tails, variational products (2 sweeps), and a smooth
+rank-saturating start (31 seeded Fourier modes of density and velocity, so
+bonds sit at chi from the first step).
+
+Prints one JSON line (rank 0):
+  value      represented MLUPS = N^3 * steps / device seconds, all ranks
+  e2e        the same through the C ABI with the populations copied host ->
+             device before and device -> host after every step
+  roofline   dominant kernel class of one profiled step against its peak
+  cpu_baseline  the CPU oracle on a bounded sample of the same step
+  clocks     nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle instead (the reference arm).
+Multi-GPU: independent replicas, one per rank (nothing is exchanged).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "porous128": dict(n=7, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
+                      chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
+                      radius=10.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
+    "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
+                      chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
+                      n_modes=0, mode_seed=0),
+}
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP32 SIMT throughput of cuBLAS SGEMM (no TF32) measured on this machine's GB300
+# (8192^3, CUDA events): the peak used for the FP32 SIMT contraction kernels.
+FP32_SIMT_MEASURED_TFLOPS = 69.8
+
+
+def geometry(w):
+    import synth
+    if w["geometry"] == "spheres":
+        return synth.sphere_pack(w["n"], w["radius"], w["solid_fraction"], w["geo_seed"])
+    return None
+
+
+def make_sim(w, solid, modes):
+    import paper_2512_07615_gb300 as tl
+    return tl.Sim(w["n"], lattice=w["lattice"], tau=w["tau"], periodic=w["periodic"], solid=solid,
+                  chi_mask=w["chi_mask"], eps_mask=w["eps_mask"], force=w["force"], chi_max=w["chi"],
+                  eps=w["eps"], precision=w["precision"], hadamard=0, sweeps=2, modes=modes)
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(w, solid, modes, budget_s=25.0):
+    """Time the oracle on the first phases of the same step (moments, rho_0,
+    Taylor 1/rho, velocity and second-order products: roundings and fits of
+    the real populations) and extrapolate to one whole step by the step's
+    counts of roundings and fits.  Returns (seconds per step, description)."""
+    import oracle.mps as M
+    import oracle.mps_lbm as ml
+    from oracle import lattice as olat
+    lat = olat.get("D3Q19" if w["lattice"] == 19 else "D3Q15")
+    # job counts of one step, from a dry run of the step's structure on 2^3 cells
+    cnt = {"round": 0, "fit": 0}
+    r0, f0 = M.lincomb_round, M.hadamard_fit
+
+    def c_round(*a, **k):
+        cnt["round"] += 1
+        return r0(*a, **k)
+
+    def c_fit(*a, **k):
+        cnt["fit"] += 1
+        return f0(*a, **k)
+
+    M.lincomb_round, M.hadamard_fit = c_round, c_fit
+    try:
+        tiny_mask = M.scale(M.ones(3), 0.1) if solid is not None else None
+        tcfg = ml.Config(1, lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=4,
+                         eps=w["eps"], hadamard="fit", mask=tiny_mask)
+        ml.step(tcfg, ml.initial_rest(tcfg))
+    finally:
+        M.lincomb_round, M.hadamard_fit = r0, f0
+    n_round, n_fit = cnt["round"], cnt["fit"]
+    # the real populations of the workload (setup, not timed)
+    cfg = ml.Config(w["n"], lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=w["chi"],
+                    eps=w["eps"], hadamard="fit", mask=None)
+    f = ml.initial_perturbed(cfg, modes) if modes is not None else ml.initial_rest(cfg)
+    t_round, t_fit = [], []
+    t_start = time.perf_counter()
+    # a1: moments
+    items = [(1.0, f[i]) for i in range(lat.Q)]
+    rho = None
+    while len(items) > 1 and time.perf_counter() - t_start < budget_s:
+        nxt = []
+        for p in range(0, len(items) - 1, 2):
+            t = time.perf_counter()
+            nxt.append((1.0, M.lincomb_round([items[p], items[p + 1]], cfg.chi, cfg.eps)))
+            t_round.append(time.perf_counter() - t)
+        if len(items) % 2:
+            nxt.append(items[-1])
+        items = nxt
+    rho = items[0][1]
+    # a3-a5 style products on the same fields
+    one = M.ones(cfg.L)
+    rho0 = M.inner_ones(rho) / float(cfg.N ** 3)
+    t = time.perf_counter()
+    drho = M.lincomb_round([(1.0, rho), (-rho0, one)], cfg.chi, cfg.eps)
+    t_round.append(time.perf_counter() - t)
+    fac = [drho] + [f[i] for i in range(1, 4)]
+    for k in range(len(fac)):
+        if time.perf_counter() - t_start > budget_s and t_fit:
+            break
+        t = time.perf_counter()
+        M.hadamard_fit(fac[k], drho, 2)
+        t_fit.append(time.perf_counter() - t)
+    per_step = n_round * float(np.mean(t_round)) + n_fit * float(np.mean(t_fit))
+    desc = ("oracle (numpy FP64) on %d roundings and %d fits of the same step (moments tree and "
+            "products of the real populations), extrapolated to the step's %d roundings and %d fits"
+            % (len(t_round), len(t_fit), n_round, n_fit))
+    return per_step, desc, time.perf_counter() - t_start
+
+
+def cpu_threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="porous128", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    N3 = float((1 << w["n"]) ** 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import synth
+    modes = synth.fourier_modes(w["n_modes"], w["mode_seed"], kmax=4, amp_rho=1e-3, amp_u=1e-3) \
+        if w["n_modes"] > 0 else None
+    solid = geometry(w)
+    config = {"workload": args.workload, "lattice": "D3Q%d" % w["lattice"], "cells": "%d^3" % (1 << w["n"]),
+              "chi_max": w["chi"], "chi_mask": w["chi_mask"] if solid is not None else None,
+              "eps": w["eps"], "tau": w["tau"], "products": "variational fit, 2 sweeps",
+              "storage": "fp32" if w["precision"] == 1 else "fp64",
+              "l2_flush": "working set > L2 (129 MB) is not claimed; each step touches ~GBs of environments"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per = []
+        desc = ""
+        for i in range(args.warmup + args.steps):
+            sec, desc, _ = oracle_sample(w, solid, modes, budget_s=8.0)
+            if i >= args.warmup:
+                per.append(sec)
+        T = float(np.sum(per))
+        val = N3 * args.steps / T / 1e6
+        out = {"impl": "reference", "metric": "represented MLUPS at fixed chi", "value": val, "unit": "MLUPS",
+               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+               "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
+                                "sample": desc},
+               "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2512_07615_gb300 as tl
+    from paper_2512_07615_gb300 import native as nat
+
+    t0 = time.time()
+    sim = make_sim(w, solid, modes)
+    setup_s = time.time() - t0
+    sim.step(args.warmup)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    with Clocks(local) as clk:
+        ms = sim.step_timed(args.steps)
+    barrier()
+    clocks = clk.summary()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    st = sim.stats()
+    value = world * N3 * args.steps / (ms / 1e3) / 1e6
+
+    # one profiled (eager, serialised) step: per kernel class time and FLOPs
+    prof = sim.profile_step()
+    total_prof_ms = sum(v["ms"] for v in prof.values())
+    dom = max(prof, key=lambda c: prof[c]["ms"])
+    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
+    fp32 = w["precision"] == 1
+    if fp32:
+        peak_tf, peak_src = FP32_SIMT_MEASURED_TFLOPS, "measured FP32 SIMT SGEMM on this pool (no TF32)"
+    else:
+        peak_tf, peak_src = 1.06, "measured FP64 DGEMM on this pool"
+    launches = max(prof[dom]["launches"], 1)
+    ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": ach / peak_tf, "traffic": None, "peak_source": peak_src,
+                "flops_per_launch": prof[dom]["flops"] / launches, "launches_per_step": prof[dom]["launches"],
+                "share_of_profiled_step": prof[dom]["ms"] / total_prof_ms if total_prof_ms else None,
+                "classes": {c: {"ms": round(v["ms"], 3), "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12
+                                                                    if v["ms"] > 0 else 0.0),
+                                "launches": v["launches"]} for c, v in prof.items()}}
+
+    # end to end through the C ABI: populations host -> device, step, device -> host
+    e2e = None
+    if not args.no_e2e:
+        pops = sim.get_populations()
+        L = 3 * w["n"]
+        ms_size = tl.tnlbm.mps_size(L, w["chi"])
+        bytes_io = w["lattice"] * (ms_size * 8 + (L + 1) * 4)
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            sim.set_populations(pops)
+            sim.step(1)
+            pops = sim.get_populations()
+        barrier()
+        el = time.perf_counter() - t
+        e2e = {"value": world * N3 * args.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sec, desc, spent = oracle_sample(w, solid, modes)
+        cpu = {"value": N3 / sec / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
+               "sample": desc, "sample_seconds": round(spent, 1)}
+
+    if rank == 0:
+        out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f32" if fp32 else "f64", "data": "synthetic", "config": config,
+               "gpu_launches": st["gpu_launches_per_step"] * args.steps,
+               "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
+               "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
+               "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out))
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

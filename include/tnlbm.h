@@ -1,0 +1,215 @@
+/*
+ * tnlbm.h - C ABI of the GB300 MPS lattice Boltzmann library (libtnlbm.so).
+ *
+ * The method (Gross et al., "Tensor Network Lattice Boltzmann Method for
+ * Data-Compressed Fluid Simulations"): every particle distribution function
+ * f_i of a D3Q19 / D3Q15 BGK lattice Boltzmann model is stored as a matrix
+ * product state (MPS, Eq. MPS) over the scale-ordered binary digits of the
+ * cell coordinates (Sec. 2.4, Eq. scale_ordering); one time step (Sec. 3.2)
+ * is carried out entirely on those encodings with no dense grid:
+ *   collision from moments, a Taylor-expanded 1/rho and compressed products
+ *   (Sec. 2.3, Sec. 3.2, App. A), streaming as shift-MPO x MPS (Sec. 2.5),
+ *   bounce-back walls and objects through mask MPS (Eqs. boundaries2, objects),
+ *   and TT-rounding of every sum (Eq. svd-move).
+ *
+ * Conventions (all entry points)
+ *   - Return 0 on success, a negative TNLBM_E_* code on failure; no exception
+ *     crosses the ABI.  tnlbm_last_error() returns a thread-local message.
+ *   - Binary sites: an N^3 lattice with N = 2^n has L = 3n sites; site k holds
+ *     bit (n-1 - k/3) of axis k%3 (axis 0 = x), most significant bits first.
+ *   - Dense fields are [x][y][z] row-major (z fastest).
+ *   - "Flat MPS layout" (host or device): for L sites and capacity cap, bond k
+ *     has capacity cap_k = cap for 0 < k < L and cap_0 = cap_L = 1; core k
+ *     occupies a slot of cap_k * 2 * cap_(k+1) elements starting at
+ *     tnlbm_mps_offset(L, cap, k); inside the slot the core is packed
+ *     [r_k][2][r_(k+1)] row-major with its realised bonds r.  Realised bonds
+ *     are an int32 array r[0..L] with r[0] = r[L] = 1.
+ *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32 buffers float.
+ *   - stream arguments are cudaStream_t values passed as void* (NULL = legacy
+ *     default stream).  Primitive calls are asynchronous on that stream unless
+ *     stated; they allocate their own scratch with cudaMalloc and free it
+ *     after synchronising the stream.
+ */
+#ifndef TNLBM_H
+#define TNLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TNLBM_OK = 0,
+  TNLBM_E_ARG = -1,      /* invalid argument or configuration            */
+  TNLBM_E_OOM = -2,      /* device or host allocation failed             */
+  TNLBM_E_CUDA = -3,     /* a CUDA runtime call failed                   */
+  TNLBM_E_TIMEOUT = -4,  /* a bounded device-side wait ran out           */
+  TNLBM_E_NOCONV = -5,   /* a Jacobi SVD hit its sweep limit             */
+  TNLBM_E_NAN = -6,      /* non-finite values detected                   */
+  TNLBM_E_CAPACITY = -7  /* a realised bond exceeded a buffer capacity   */
+};
+
+enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1 };
+enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
+enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1 };
+
+/* ------------------------------------------------------------ simulation */
+
+typedef struct tnlbm_sim tnlbm_sim; /* opaque; owns all its device memory */
+
+typedef struct {
+  int n_per_axis;          /* bits per axis n, N = 2^n, 2 <= n <= 10           */
+  int lattice;             /* TNLBM_D3Q19 or TNLBM_D3Q15 (Sec. 3.1)            */
+  double tau;              /* BGK relaxation time (Eq. collision), > 0.5       */
+  int periodic[3];         /* per axis: 1 = cyclic shift S, 0 = wall: non-cyclic
+                              shift plus halfway bounce-back (Eq. boundaries2)   */
+  const uint8_t *solid;    /* host N^3 voxels [x][y][z], 1 = solid, or NULL;
+                              copied during create; compressed on the GPU by
+                              TT-SVD (Eq. svd-comp) to chi_mask / eps_mask      */
+  int chi_mask;            /* bond cap of the object mask MPS                  */
+  double eps_mask;         /* relative tolerance of the mask TT-SVD            */
+  const double *mask_cores;/* alternative to solid: host mask MPS m_O in flat
+                              layout (FP64, capacity mask_cap), or NULL         */
+  const int *mask_ranks;   /* its realised bonds r[0..L]                       */
+  int mask_cap;
+  double force[3];         /* body force density F (App. A), lattice units     */
+  int chi_max;             /* bond cap chi of every rounding (Sec. 2.1)        */
+  double eps;              /* relative rounding tolerance: keep the smallest
+                              rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
+  int precision;           /* TNLBM_FP64 or TNLBM_FP32                         */
+  int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default) or _EXACT
+                              (Eq. mul followed by a rounding)                  */
+  int sweeps;              /* round trips of the product fit (Sec. 2.3: 2)     */
+  int n_modes;             /* 0: start at rest, f_i = w_i (1 - m_O);  > 0:
+                              f_i = w_i (1 + sum_m (a_rho + 3 c_i.a_u) cos(2 pi
+                              k.x/N + phase)), rounded once                     */
+  const double *modes;     /* host [n_modes][8]: kx ky kz phase a_rho a_ux a_uy a_uz */
+  int max_jobs_in_flight;  /* 0 = default; caps rounding CTAs per launch        */
+} tnlbm_config;
+
+typedef struct {
+  int64_t steps;             /* steps taken so far                               */
+  int max_bond;              /* largest realised bond over all populations       */
+  double mean_bond;          /* mean realised bond over all bonds/populations    */
+  double nvps;               /* sum over populations of sum_k r_k*2*r_(k+1)      */
+  double compression_ratio;  /* Q*N^3 / nvps                                     */
+  double rho0;               /* last mean density rho_0 (Sec. 3.2)               */
+  int status;                /* device status word (0 = fine)                    */
+  int gpu_launches_per_step; /* kernels launched by one tnlbm_step(1)            */
+} tnlbm_stats;
+
+/* Build a simulation: shift MPOs, mask MPS, initial populations, and a CUDA
+ * graph of one time step.  Uses the current CUDA device.  On failure *out is
+ * NULL and everything allocated is released. */
+int tnlbm_create(const tnlbm_config *cfg, tnlbm_sim **out);
+
+/* Advance k >= 0 time steps (Sec. 3.2, Eq. evolution); synchronous. */
+int tnlbm_step(tnlbm_sim *s, int k);
+
+/* Contract the populations to dense fields (host, caller-owned, FP64):
+ * rho[N^3] = sum_i f_i and u[3][N^3] = (sum_i c_i f_i + F (1 - m_O)/2) / rho
+ * where rho > 0.5, else 0.  Either pointer may be NULL.  Synchronous. */
+int tnlbm_macroscopic(tnlbm_sim *s, double *rho, double *u);
+
+/* Populations as MPS: host buffers of Q * tnlbm_mps_size(L, chi_max) doubles
+ * (flat layout, capacity chi_max, population-major) and Q*(L+1) ints.
+ * get = checkpoint, set = resume / custom initial state. Synchronous. */
+int tnlbm_get_populations(tnlbm_sim *s, double *cores, int *ranks);
+int tnlbm_set_populations(tnlbm_sim *s, const double *cores, const int *ranks);
+
+int tnlbm_stats_get(tnlbm_sim *s, tnlbm_stats *out);
+
+/* Advance k steps through the captured graph and return the device time of
+ * the k launches in *ms (CUDA events on the simulation's stream). */
+int tnlbm_step_timed(tnlbm_sim *s, int k, double *ms);
+
+/* Kernel classes reported by tnlbm_profile_step (array index). */
+enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_MISC = 3,
+       TNLBM_K_RHO0 = 4, TNLBM_K_COPY = 5, TNLBM_K_COUNT = 6 };
+
+/* Advance one step with eager (non-graph), serialised launches and report per
+ * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
+ * launch), algorithmic FLOPs flops[] (counted on the device from the realised
+ * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[]. */
+int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches);
+int tnlbm_destroy(tnlbm_sim *s); /* NULL-safe */
+const char *tnlbm_last_error(void);
+
+/* ------------------------------------------------------------ layout helpers */
+
+size_t tnlbm_mps_size(int L, int cap);      /* elements of one flat MPS  */
+size_t tnlbm_mps_offset(int L, int cap, int k); /* element offset of core k */
+
+/* ------------------------------------------------------------ primitives
+ * Batched operations on caller-owned DEVICE buffers in the flat layout.
+ * Pointer arrays ("const void *const *src" etc.) are HOST arrays of length
+ * `batch` holding device pointers.  All MPS of one call have L = 3*n_bits. */
+
+enum {
+  TNLBM_TERM_PLAIN = 0, /* coef * X                                           */
+  TNLBM_TERM_SHIFT = 1, /* coef * S X: 1-D shift MPO along `axis` (Sec. 2.5),
+                           (S X)(x) = X(x + offset e_axis), offset = +1 / -1,
+                           cyclic (S) or non-cyclic (S^, zero where x+offset
+                           leaves the domain)                                 */
+  TNLBM_TERM_MASK1 = 2, /* coef * (m . X), m a rank-1 MPS given by per-site
+                           2-vectors mask[k][2] (exact product, Eq. mul)      */
+  TNLBM_TERM_KRON = 3,  /* coef * (X . Y) exact product by Eq. (mul)          */
+  TNLBM_TERM_ONES = 4   /* coef * 1, the rank-1 all-ones MPS                  */
+};
+
+typedef struct {
+  int kind;
+  double coef;
+  const void *x; const int *x_ranks; int x_cap; /* device MPS (not for ONES) */
+  const void *y; const int *y_ranks; int y_cap; /* KRON second factor        */
+  int axis, offset, cyclic;                     /* SHIFT                     */
+  const double *mask;                           /* MASK1: host [L][2]        */
+} tnlbm_term;
+
+/* dst[b] = round(sum_t terms[b*nterms + t]) : block-diagonal sum (Eq. add) of
+ * the (exactly formed) terms, then a left-orthogonalising QR sweep and a
+ * right-to-left truncated SVD sweep (Eq. svd-move) with bond cap chi_max and
+ * relative tolerance eps.  dst capacity must be >= chi_max. */
+int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms,
+                        const tnlbm_term *terms, void *const *dst,
+                        int *const *dst_ranks, int dst_cap, int chi_max,
+                        double eps, void *stream);
+
+/* dst[b] = the single term, formed exactly without rounding (bond grows:
+ * SHIFT doubles it inside the axis span, KRON multiplies bonds). */
+int tnlbm_materialize(int precision, int n_bits, int batch,
+                      const tnlbm_term *terms, void *const *dst,
+                      int *const *dst_ranks, int dst_cap, void *stream);
+
+/* A[b] ~ B[b] . C[b] by the single-site variational fit of Sec. 2.3: candidate
+ * A = B (bonds unchanged), `sweeps` round trips of local updates and QR/LQ
+ * centre shifts.  A must have capacity >= B's. */
+int tnlbm_hadamard_fit(int precision, int n_bits, int batch,
+                       const void *const *B, const int *const *rB, int capB,
+                       const void *const *C, const int *const *rC, int capC,
+                       void *const *A, int *const *rA, int capA, int sweeps,
+                       void *stream);
+
+/* out[b] (device doubles) = <X[b], 1>, the sum of all entries (Sec. 3.2). */
+int tnlbm_inner_ones(int precision, int n_bits, int batch,
+                     const void *const *X, const int *const *rX, int capX,
+                     double *out, void *stream);
+
+/* dense[x][y][z] (device, N^3 elements of the precision's type) = contraction
+ * of the MPS (Eq. MPS). */
+int tnlbm_to_dense(int precision, int n_bits, const void *X, const int *rX,
+                   int capX, void *dense, void *stream);
+
+/* TT-SVD of a dense device field [x][y][z] into an MPS (Eq. svd-comp, the mask
+ * builder), truncating each bond to chi_max / eps.  The singular values come
+ * from FP64 Gram matrices, so tails below ~1e-8 of the norm are not resolved. */
+int tnlbm_from_dense(int precision, int n_bits, const void *dense, void *dst,
+                     int *dst_ranks, int dst_cap, int chi_max, double eps,
+                     void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TNLBM_H */

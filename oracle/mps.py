@@ -211,19 +211,29 @@ def inner_ones(A):
 
 # ---------------------------------------------------------------- Sec. 2.3
 
+# Each contraction below is the plain sum written in three pairwise steps (the
+# physical index s is shared by three tensors, so a single einsum call would
+# not split it and would cost chi^6 instead of chi^4).
+
 def _env_left(EL, A, B, C):
     # EL'[x,y,z] = sum_{a,b,g,s} EL[a,b,g] A[a,s,x] B[b,s,y] C[g,s,z]
-    return np.einsum("abg,asx,bsy,gsz->xyz", EL, A, B, C, optimize=True)
+    t = np.einsum("abg,asx->bgsx", EL, A, optimize=True)
+    t = np.einsum("bgsx,bsy->gsxy", t, B, optimize=True)
+    return np.einsum("gsxy,gsz->xyz", t, C, optimize=True)
 
 
 def _env_right(ER, A, B, C):
     # ER'[a,b,g] = sum_{s,x,y,z} A[a,s,x] B[b,s,y] C[g,s,z] ER[x,y,z]
-    return np.einsum("asx,bsy,gsz,xyz->abg", A, B, C, ER, optimize=True)
+    t = np.einsum("gsz,xyz->gsxy", C, ER, optimize=True)
+    t = np.einsum("bsy,gsxy->bgsx", B, t, optimize=True)
+    return np.einsum("asx,bgsx->abg", A, t, optimize=True)
 
 
 def _local(EL, B, C, ER):
     # optimal centre: A_c[a,s,x] = sum EL[a,b,g] B[b,s,y] C[g,s,z] ER[x,y,z]
-    return np.einsum("abg,bsy,gsz,xyz->asx", EL, B, C, ER, optimize=True)
+    t = np.einsum("abg,bsy->agsy", EL, B, optimize=True)
+    t = np.einsum("agsy,gsz->asyz", t, C, optimize=True)
+    return np.einsum("asyz,xyz->asx", t, ER, optimize=True)
 
 
 def right_orthogonalize(cores):

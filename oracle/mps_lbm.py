@@ -17,7 +17,8 @@ Every population f_i is an MPS on L = 3n binary sites (Sec. 2.4).  One step:
                  shift an exact MPO (Sec. 2.5) followed by a rounding; on wall axes
                  the non-cyclic shift is used and the last rounding also adds the
                  halfway bounce-back term m_B,i * f*_opp(i)     (Eq. boundaries2)
- a8 objects      g_i = f_i * m_O;  f_i <- f_i - g_i + S(c_i) g_opp(i)  (Eq. objects)
+ a8 objects      g_i = f_i * m_O;  f_i <- (f_i - g_i) + S(c_i) g_opp(i)  (Eq. objects),
+                 two rounded pairwise sums
  a9 rounding     every sum above is rounded with oracle.mps.round_mps
 
 Products "*" use the single-site fit of Sec. 2.3 with the first factor as the
@@ -281,7 +282,8 @@ def step(cfg, f):
         for d in range(3):
             if c[d] != 0:
                 h = _R(cfg, [(1.0, _shift(cfg, h, d, c[d]))])
-        out.append(_R(cfg, [(1.0, fs[i]), (-1.0, g[i]), (1.0, h)]))
+        t = _R(cfg, [(1.0, fs[i]), (-1.0, g[i])])
+        out.append(_R(cfg, [(1.0, t), (1.0, h)]))
     return out
 
 

@@ -1,0 +1,1178 @@
+// C ABI of libtnlbm: the simulation object (one MPS-LBM time step captured as
+// a CUDA graph) and the batched MPS primitives.
+//
+// The step (Sec. 3.2) is written as a DAG of MPS nodes; every node is produced
+// by a rounding job (a rounded linear combination of exactly formed terms) or a
+// product fit (Sec. 2.3).  Jobs are grouped by dependency level; a level runs
+// its rounding jobs in one launch and its fits on a second stream, so the
+// whole step is a fork-join graph.  Order of the linear combinations:
+//   a1 moments as balanced pairwise trees; a6 shared prefix sums
+//   E0 = ((rho - 1.5 Pxx) - 1.5 Pyy) - 1.5 Pzz, second-order prefixes (diagonal
+//   terms xx, yy, zz first, then xy, xz, yz), sign-normalised first-order sums;
+//   a7 one axis shift at a time (x, y, z) with the bounce-back term added in the
+//   last rounding; a8 g_i = f_i . m_O used in both object terms, and the object
+//   update (f_i - g_i) + S g_opp(i) as two pairwise rounded sums.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fit.cuh"
+#include "internal.cuh"
+
+namespace tn {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+  return TNLBM_E_CUDA;
+}
+
+static int status_to_code(const int* st8) {
+  const int st = st8[0];
+  if (st & ST_NOCONV && !(st & (ST_CAPACITY | ST_NAN | ST_TIMEOUT))) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "Jacobi SVD reached its sweep limit (job %d, site %d, %d columns of length %d)",
+             st8[2], st8[3], st8[4], st8[5]);
+    set_error(buf);
+    return TNLBM_E_NOCONV;
+  }
+  if (st & ST_CAPACITY) { set_error("a realised bond exceeded a buffer capacity"); return TNLBM_E_CAPACITY; }
+  if (st & ST_NAN) { set_error("non-finite values in a rounding"); return TNLBM_E_NAN; }
+  if (st & ST_TIMEOUT) { set_error("bounded device wait ran out"); return TNLBM_E_TIMEOUT; }
+  if (st & ST_NOCONV) { set_error("Jacobi SVD reached its sweep limit"); return TNLBM_E_NOCONV; }
+  return 0;
+}
+
+// ---------------------------------------------------------------- lattices
+struct LatticeDef {
+  int Q;
+  int c[19][3];
+  double w[19];
+  int opp[19];
+};
+
+static LatticeDef make_lattice(int q) {
+  LatticeDef L{};
+  static const int c19[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0},  {0, 1, 0},  {0, -1, 0},
+                                 {0, 0, 1},  {0, 0, -1}, {1, 1, 0},   {-1, -1, 0}, {1, -1, 0},
+                                 {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                 {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+  static const int c15[15][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                                 {0, 0, 1},  {0, 0, -1},  {1, 1, 1},  {-1, -1, -1}, {1, 1, -1},
+                                 {-1, -1, 1}, {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1},  {1, -1, -1}};
+  L.Q = q;
+  for (int i = 0; i < q; ++i) {
+    for (int d = 0; d < 3; ++d) L.c[i][d] = (q == 19) ? c19[i][d] : c15[i][d];
+    if (q == 19) L.w[i] = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    else L.w[i] = i == 0 ? 2.0 / 9.0 : (i < 7 ? 1.0 / 9.0 : 1.0 / 72.0);
+    L.opp[i] = i == 0 ? 0 : ((i % 2 == 1) ? i + 1 : i - 1);
+  }
+  return L;
+}
+
+// ---------------------------------------------------------------- device arena
+struct Arena {
+  std::vector<void*> ptrs;
+  ~Arena() { for (void* p : ptrs) cudaFree(p); }
+  void* alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    return p;
+  }
+};
+
+// ---------------------------------------------------------------- step DAG
+struct TermSpec {       // host-side description of a term, resolved to MpsRef at build time
+  int kind = T_PLAIN;
+  int x = -1, y = -1;   // node ids
+  double coef = 1.0;
+  int coef_slot = -1;
+  int axis = 0, offset = 0, cyclic = 1;
+  int mask_id = -1;
+};
+
+struct JobSpec {
+  int kind;             // 0 rounding, 1 fit, 2 rho0 scalar
+  int out;              // node id
+  std::vector<TermSpec> terms;
+  int b = -1, c = -1;   // fit factors
+  int level = 0;
+};
+
+}  // namespace tn
+
+using namespace tn;
+
+struct tnlbm_sim {
+  tnlbm_config cfg{};
+  int n = 0, L = 0, N = 0, prec = 0;
+  size_t esz = 8;
+  LatticeDef lat{};
+  Arena arena;
+  cudaStream_t s0 = nullptr, s1 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  // nodes
+  std::vector<MpsRef> nodes;
+  std::vector<int> node_level;
+  int scal_node = -1;
+  std::vector<int> f_state, f_next;
+  int mask_node = -1;
+  int rho_node = -1;
+  double n_fluid = 0.0;
+  // masks (rank-1 wall planes) [id][TN_MAXL][2]
+  std::vector<double> mask_vecs;
+  void* d_masks = nullptr;
+  double* d_scal = nullptr;
+  int* d_status = nullptr;
+  // jobs per level
+  std::vector<JobSpec> specs;
+  struct Level {
+    std::vector<RoundJob> rj;
+    std::vector<FitJob> fj;
+    RoundJob* d_rj = nullptr;
+    FitJob* d_fj = nullptr;
+    bool has_rho0 = false;
+  };
+  std::vector<Level> levels;
+  MpsRef* d_rho_ref = nullptr;
+  MpsRef* d_copy_src = nullptr;
+  MpsRef* d_copy_dst = nullptr;
+  int launches_per_step = 0;
+  int64_t steps = 0;
+  int pending_status = 0;
+};
+
+namespace tn {
+
+static int new_node(tnlbm_sim* s, int cap, int level) {
+  MpsRef m{};
+  m.cap = cap;
+  m.base = s->arena.alloc(mps_size(s->L, cap) * s->esz);
+  m.ranks = (int*)s->arena.alloc((s->L + 1) * sizeof(int));
+  if (!m.base || !m.ranks) return -1;
+  std::vector<int> ones(s->L + 1, 1);
+  cudaMemcpy(m.ranks, ones.data(), ones.size() * sizeof(int), cudaMemcpyHostToDevice);
+  cudaMemset(m.base, 0, mps_size(s->L, cap) * s->esz);
+  s->nodes.push_back(m);
+  s->node_level.push_back(level);
+  return (int)s->nodes.size() - 1;
+}
+
+struct Builder {
+  tnlbm_sim* s;
+  bool oom = false;
+  int chi() const { return s->cfg.chi_max; }
+
+  int level_of_terms(const std::vector<TermSpec>& ts) {
+    int lv = 0;
+    for (const TermSpec& t : ts) {
+      if (t.x >= 0) lv = std::max(lv, s->node_level[t.x]);
+      if (t.y >= 0) lv = std::max(lv, s->node_level[t.y]);
+      if (t.coef_slot >= 0) lv = std::max(lv, s->node_level[s->scal_node]);
+    }
+    return lv + 1;
+  }
+  int R(const std::vector<TermSpec>& ts) {
+    int lv = level_of_terms(ts);
+    int out = new_node(s, chi(), lv);
+    if (out < 0) { oom = true; return -1; }
+    JobSpec j;
+    j.kind = 0; j.out = out; j.terms = ts; j.level = lv;
+    s->specs.push_back(j);
+    return out;
+  }
+  int H(int b, int c) {
+    if (s->cfg.hadamard == TNLBM_HADAMARD_EXACT) {
+      TermSpec t; t.kind = T_KRON; t.x = b; t.y = c;
+      return R({t});
+    }
+    int lv = std::max(s->node_level[b], s->node_level[c]) + 1;
+    int out = new_node(s, s->nodes[b].cap, lv);
+    if (out < 0) { oom = true; return -1; }
+    JobSpec j;
+    j.kind = 1; j.out = out; j.b = b; j.c = c; j.level = lv;
+    s->specs.push_back(j);
+    return out;
+  }
+  static TermSpec P(int x, double c, int slot = -1) {
+    TermSpec t; t.kind = T_PLAIN; t.x = x; t.coef = c; t.coef_slot = slot; return t;
+  }
+  static TermSpec ONE(double c, int slot = -1) {
+    TermSpec t; t.kind = T_ONES; t.coef = c; t.coef_slot = slot; return t;
+  }
+  TermSpec SH(int x, int axis, int cd) {
+    TermSpec t; t.kind = T_SHIFT; t.x = x; t.axis = axis; t.offset = -cd;
+    t.cyclic = s->cfg.periodic[axis] ? 1 : 0;
+    return t;
+  }
+  int mask_plane_product(const std::vector<int>& axes, const int* c) {
+    // rank-1 product of plane indicators x_d = 0 (c_d > 0) or N-1 (c_d < 0)
+    int id = (int)(s->mask_vecs.size() / (TN_MAXL * 2));
+    s->mask_vecs.resize(s->mask_vecs.size() + TN_MAXL * 2, 1.0);
+    double* v = &s->mask_vecs[(size_t)id * TN_MAXL * 2];
+    for (int k = 0; k < s->L; ++k) {
+      int d = k % 3;
+      if (std::find(axes.begin(), axes.end(), d) != axes.end()) {
+        v[2 * k + 0] = c[d] > 0 ? 1.0 : 0.0;
+        v[2 * k + 1] = c[d] > 0 ? 0.0 : 1.0;
+      }
+    }
+    return id;
+  }
+
+  int tree_sum(std::vector<TermSpec> items) {
+    while (items.size() > 1) {
+      std::vector<TermSpec> nxt;
+      for (size_t p = 0; p + 1 < items.size(); p += 2) nxt.push_back(P(R({items[p], items[p + 1]}), 1.0));
+      if (items.size() % 2 == 1) nxt.push_back(items.back());
+      items = nxt;
+    }
+    if (items[0].coef == 1.0) return items[0].x;
+    return R({items[0]});
+  }
+
+  void build_step() {
+    tnlbm_sim& S = *s;
+    const LatticeDef& lat = S.lat;
+    const int Q = lat.Q;
+    const double tau = S.cfg.tau, omega = 1.0 / tau;
+    // a1 moments
+    std::vector<TermSpec> it;
+    for (int i = 0; i < Q; ++i) it.push_back(P(S.f_state[i], 1.0));
+    int rho = tree_sum(it);
+    S.rho_node = rho;
+    int j[3];
+    for (int d = 0; d < 3; ++d) {
+      std::vector<TermSpec> v;
+      for (int i = 0; i < Q; ++i)
+        if (lat.c[i][d] != 0) v.push_back(P(S.f_state[i], (double)lat.c[i][d]));
+      j[d] = tree_sum(v);
+    }
+    // a2 rho_0 (a scalar pseudo-node)
+    S.scal_node = new_node(s, 1, S.node_level[rho] + 1);
+    {
+      JobSpec js; js.kind = 2; js.out = S.scal_node; js.b = rho; js.level = S.node_level[S.scal_node];
+      S.specs.push_back(js);
+    }
+    // a3
+    int drho = R({P(rho, 1.0), ONE(1.0, SC_NEG_RHO0)});
+    int sq = H(drho, drho);
+    int inv = R({ONE(1.0, SC_INV1), P(drho, 1.0, SC_INV2), P(sq, 1.0, SC_INV3)});
+    // a4
+    int Jt[3];
+    for (int d = 0; d < 3; ++d) {
+      const double F = S.cfg.force[d];
+      if (F == 0.0) { Jt[d] = j[d]; continue; }
+      std::vector<TermSpec> ts = {P(j[d], 1.0), ONE(tau * F)};
+      if (S.mask_node >= 0) ts.push_back(P(S.mask_node, -tau * F));
+      Jt[d] = R(ts);
+    }
+    int u[3];
+    for (int d = 0; d < 3; ++d) u[d] = H(Jt[d], inv);
+    // a5
+    int Pm[3][3];
+    for (int d = 0; d < 3; ++d)
+      for (int e = d; e < 3; ++e) Pm[d][e] = H(Jt[d], u[e]);
+    // a6
+    int E0 = rho;
+    for (int d = 0; d < 3; ++d) E0 = R({P(E0, 1.0), P(Pm[d][d], -1.5)});
+    std::map<std::vector<std::pair<int, double>>, int> qcache;   // key: (de code, kappa)
+    std::map<std::vector<std::pair<int, double>>, int> vcache;
+    auto qchain = [&](auto&& self, const std::vector<std::pair<int, double>>& key) -> int {
+      if (key.empty()) return E0;
+      auto itq = qcache.find(key);
+      if (itq != qcache.end()) return itq->second;
+      std::vector<std::pair<int, double>> pre(key.begin(), key.end() - 1);
+      int prev = self(self, pre);
+      int de = key.back().first;
+      int out = R({P(prev, 1.0), P(Pm[de / 3][de % 3], key.back().second)});
+      qcache[key] = out;
+      return out;
+    };
+    // returns term (coef, node) for a first-order key
+    auto vchain = [&](auto&& self, const std::vector<std::pair<int, double>>& key) -> TermSpec {
+      if (key.size() == 1) return P(Jt[key[0].first], key[0].second);
+      auto itv = vcache.find(key);
+      if (itv != vcache.end()) return P(itv->second, 1.0);
+      std::vector<std::pair<int, double>> pre(key.begin(), key.end() - 1);
+      TermSpec prev = self(self, pre);
+      int out = R({prev, P(Jt[key.back().first], key.back().second)});
+      vcache[key] = out;
+      return P(out, 1.0);
+    };
+    std::vector<int> fstar(Q);
+    for (int i = 0; i < Q; ++i) {
+      const int* c = lat.c[i];
+      std::vector<std::pair<int, double>> qk;
+      for (int d = 0; d < 3; ++d)
+        if (c[d] != 0) qk.push_back({d * 3 + d, 4.5 * c[d] * c[d]});
+      const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+      for (auto& pr : pairs)
+        if (c[pr[0]] != 0 && c[pr[1]] != 0) qk.push_back({pr[0] * 3 + pr[1], 9.0 * c[pr[0]] * c[pr[1]]});
+      int Qi = qchain(qchain, qk);
+      std::vector<std::pair<int, double>> first;
+      for (int d = 0; d < 3; ++d)
+        if (c[d] != 0) first.push_back({d, 3.0 * c[d]});
+      int Y;
+      if (!first.empty()) {
+        const double sigma = first[0].second > 0 ? 1.0 : -1.0;
+        for (auto& p : first) p.second *= sigma;
+        TermSpec v = vchain(vchain, first);
+        v.coef *= sigma;
+        Y = R({P(Qi, 1.0), v});
+      } else {
+        Y = Qi;
+      }
+      fstar[i] = R({P(S.f_state[i], 1.0 - omega), P(Y, omega * lat.w[i])});
+    }
+    // a7 streaming
+    std::vector<int> fs(Q);
+    for (int i = 0; i < Q; ++i) {
+      const int* c = lat.c[i];
+      std::vector<int> axes;
+      for (int d = 0; d < 3; ++d) if (c[d] != 0) axes.push_back(d);
+      int x = fstar[i];
+      std::vector<int> W;
+      for (int d : axes) if (!S.cfg.periodic[d]) W.push_back(d);
+      for (size_t t = 0; t < axes.size(); ++t) {
+        std::vector<TermSpec> ts = {SH(x, axes[t], c[axes[t]])};
+        if (t + 1 == axes.size()) {
+          for (int bits = 1; bits < (1 << W.size()); ++bits) {
+            std::vector<int> sub;
+            for (size_t q = 0; q < W.size(); ++q) if (bits >> q & 1) sub.push_back(W[q]);
+            TermSpec m; m.kind = T_MASK1; m.x = fstar[lat.opp[i]];
+            m.coef = (sub.size() % 2 == 1) ? 1.0 : -1.0;
+            m.mask_id = mask_plane_product(sub, c);
+            ts.push_back(m);
+          }
+        }
+        x = R(ts);
+      }
+      fs[i] = x;
+    }
+    std::vector<int> out = fs;
+    if (S.mask_node >= 0) {
+      // a8 objects
+      std::vector<int> g(Q, -1);
+      for (int i = 1; i < Q; ++i) g[i] = H(fs[i], S.mask_node);
+      for (int i = 1; i < Q; ++i) {
+        const int* c = lat.c[i];
+        int h = g[lat.opp[i]];
+        for (int d = 0; d < 3; ++d) if (c[d] != 0) h = R({SH(h, d, c[d])});
+        int t = R({P(fs[i], 1.0), P(g[i], -1.0)});
+        out[i] = R({P(t, 1.0), P(h, 1.0)});
+      }
+    }
+    S.f_next = out;
+  }
+};
+
+template <typename T>
+static int upload_levels(tnlbm_sim* s) {
+  // group specs by level, materialise RoundJobs / FitJobs with scratch shared across levels
+  int maxlv = 0;
+  for (auto& j : s->specs) maxlv = std::max(maxlv, j.level);
+  s->levels.assign(maxlv + 1, tnlbm_sim::Level{});
+  size_t round_scr = 0, fit_scr = 0;
+  std::vector<size_t> lvl_round(maxlv + 1, 0), lvl_fit(maxlv + 1, 0);
+  for (auto& js : s->specs) {
+    tnlbm_sim::Level& lv = s->levels[js.level];
+    if (js.kind == 2) { lv.has_rho0 = true; continue; }
+    if (js.kind == 0) {
+      RoundJob rj{};
+      rj.nterms = (int)js.terms.size();
+      if (rj.nterms > TN_MAXT) { set_error("too many terms in a rounding job"); return TNLBM_E_ARG; }
+      rj.chi = s->cfg.chi_max;
+      rj.eps = s->cfg.eps;
+      for (int t = 0; t < rj.nterms; ++t) {
+        const TermSpec& ts = js.terms[t];
+        Term& tm = rj.t[t];
+        tm.kind = ts.kind; tm.axis = ts.axis; tm.offset = ts.offset; tm.cyclic = ts.cyclic;
+        tm.coef = ts.coef; tm.coef_slot = ts.coef_slot; tm.mask_id = ts.mask_id;
+        if (ts.x >= 0) tm.x = s->nodes[ts.x];
+        if (ts.y >= 0) tm.y = s->nodes[ts.y];
+      }
+      rj.dst = s->nodes[js.out];
+      plan_round_job(rj, s->L, s->n, sizeof(T));
+      lvl_round[js.level] += rj.lay.total;
+      lv.rj.push_back(rj);
+    } else {
+      FitJob fj{};
+      fj.A = s->nodes[js.out];
+      fj.B = s->nodes[js.b];
+      fj.C = s->nodes[js.c];
+      size_t env, xs, ys, ab, q;
+      plan_fit_job(fj, s->L, &env, &xs, &ys, &ab, &q);
+      fj.env_stride = env;
+      fj.qscr_stride = q;
+      lvl_fit[js.level] += 2 * (s->L + 1) * env + xs + ys + ab + 4 * q;
+      lv.fj.push_back(fj);
+    }
+  }
+  for (int l = 0; l <= maxlv; ++l) {
+    round_scr = std::max(round_scr, lvl_round[l]);
+    fit_scr = std::max(fit_scr, lvl_fit[l]);
+  }
+  T* rbase = (T*)s->arena.alloc(round_scr * sizeof(T));
+  T* fbase = (T*)s->arena.alloc(fit_scr * sizeof(T));
+  if (!rbase || !fbase) { set_error("out of device memory for scratch"); return TNLBM_E_OOM; }
+  for (auto& lv : s->levels) {
+    size_t o = 0;
+    for (auto& rj : lv.rj) { rj.scratch = rbase + o; o += rj.lay.total; }
+    o = 0;
+    for (auto& fj : lv.fj) {
+      size_t env, xs, ys, ab, q;
+      plan_fit_job(fj, s->L, &env, &xs, &ys, &ab, &q);
+      fj.env_l = fbase + o; o += (s->L + 1) * env;
+      fj.env_r = fbase + o; o += (s->L + 1) * env;
+      fj.x = fbase + o; o += xs;
+      fj.y = fbase + o; o += ys;
+      fj.abuf = fbase + o; o += ab;
+      fj.qscr = fbase + o; o += 4 * q;
+    }
+    if (!lv.rj.empty()) {
+      lv.d_rj = (RoundJob*)s->arena.alloc(lv.rj.size() * sizeof(RoundJob));
+      if (!lv.d_rj) return TNLBM_E_OOM;
+      cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice);
+    }
+    if (!lv.fj.empty()) {
+      lv.d_fj = (FitJob*)s->arena.alloc(lv.fj.size() * sizeof(FitJob));
+      if (!lv.d_fj) return TNLBM_E_OOM;
+      cudaMemcpy(lv.d_fj, lv.fj.data(), lv.fj.size() * sizeof(FitJob), cudaMemcpyHostToDevice);
+    }
+  }
+  return 0;
+}
+
+template <typename T>
+static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
+  int n = 0;
+  double* ctr = prof ? prof->d_ctr : nullptr;
+  for (auto& lv : s->levels) {
+    if (lv.has_rho0) {
+      launch_rho0<T>(s->d_rho_ref, s->L, s->n_fluid, s->d_scal, s->s0);
+      if (prof) prof->mark(C_RHO0);
+      ++n;
+    }
+    const bool both = !prof && !lv.rj.empty() && !lv.fj.empty();   // profiled runs stay serial
+    if (both) {
+      cudaEventRecord(s->ev_fork, s->s0);
+      cudaStreamWaitEvent(s->s1, s->ev_fork, 0);
+    }
+    if (!lv.fj.empty())
+      n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof);
+    if (!lv.rj.empty()) {
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal,
+                      s->d_status, s->s0, ctr);
+      if (prof) prof->mark(C_ROUND);
+      ++n;
+    }
+    if (both) {
+      cudaEventRecord(s->ev_join, s->s1);
+      cudaStreamWaitEvent(s->s0, s->ev_join, 0);
+    }
+  }
+  launch_copy<T>(s->d_copy_src, s->d_copy_dst, s->lat.Q, s->L, s->s0);
+  if (prof) prof->mark(C_COPY);
+  ++n;
+  *launches = n;
+  return 0;
+}
+
+// one-off rounding jobs (initial states): terms over nodes
+template <typename T>
+static int run_round_now(tnlbm_sim* s, std::vector<RoundJob>& jobs) {
+  if (jobs.empty()) return 0;
+  size_t tot = 0;
+  for (auto& j : jobs) { plan_round_job(j, s->L, s->n, sizeof(T)); tot += j.lay.total; }
+  T* scr = nullptr;
+  RoundJob* dj = nullptr;
+  if (cudaMalloc(&scr, std::max<size_t>(tot, 1) * sizeof(T)) != cudaSuccess) return TNLBM_E_OOM;
+  size_t o = 0;
+  for (auto& j : jobs) { j.scratch = scr + o; o += j.lay.total; }
+  if (cudaMalloc(&dj, jobs.size() * sizeof(RoundJob)) != cudaSuccess) { cudaFree(scr); return TNLBM_E_OOM; }
+  cudaMemcpy(dj, jobs.data(), jobs.size() * sizeof(RoundJob), cudaMemcpyHostToDevice);
+  launch_round<T>(dj, (int)jobs.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal, s->d_status, s->s0);
+  cudaError_t e = cudaStreamSynchronize(s->s0);
+  cudaFree(scr);
+  cudaFree(dj);
+  if (e != cudaSuccess) return cuda_fail(e, "initial rounding");
+  return 0;
+}
+
+static void mode_cores(int n_bits, const double* row, std::vector<std::vector<double>>& cores) {
+  // exact rank-2 MPS of cos(2 pi k.x / N + phase): each site rotates the running
+  // (cos, sin) pair by its bit's phase
+  const int L = 3 * n_bits;
+  const double N = (double)(1 << n_bits);
+  cores.assign(L, {});
+  for (int s = 0; s < L; ++s) {
+    const int a = s % 3, lev = s / 3;
+    double rot[2][2][2];   // [b][row][col]
+    for (int b = 0; b < 2; ++b) {
+      const double th = 2.0 * M_PI * row[a] * (double)(1 << (n_bits - 1 - lev)) * b / N;
+      rot[b][0][0] = cos(th); rot[b][0][1] = sin(th);
+      rot[b][1][0] = -sin(th); rot[b][1][1] = cos(th);
+    }
+    const int r0 = s == 0 ? 1 : 2, r1 = s == L - 1 ? 1 : 2;
+    std::vector<double>& c = cores[s];
+    c.assign((size_t)r0 * 2 * r1, 0.0);
+    for (int i = 0; i < r0; ++i)
+      for (int b = 0; b < 2; ++b)
+        for (int jj = 0; jj < r1; ++jj) {
+          double v;
+          if (s == 0) v = cos(row[3]) * rot[b][0][jj] + sin(row[3]) * rot[b][1][jj];
+          else v = rot[b][i][jj];
+          c[((size_t)i * 2 + b) * r1 + jj] = v;
+        }
+  }
+}
+
+template <typename T>
+static int upload_host_mps(tnlbm_sim* s, int node, const double* cores, const int* ranks, int cap_src) {
+  const MpsRef& m = s->nodes[node];
+  std::vector<T> buf(mps_size(s->L, m.cap), (T)0);
+  for (int k = 0; k < s->L; ++k) {
+    const int r0 = ranks[k], r1 = ranks[k + 1];
+    if (r0 > bond_cap(s->L, m.cap, k) || r1 > bond_cap(s->L, m.cap, k + 1) || r0 < 1 || r1 < 1) {
+      set_error("MPS bond exceeds capacity");
+      return TNLBM_E_CAPACITY;
+    }
+    const double* src = cores + core_offset(s->L, cap_src, k);
+    T* dst = buf.data() + core_offset(s->L, m.cap, k);
+    for (int i = 0; i < r0 * 2 * r1; ++i) dst[i] = (T)src[i];
+  }
+  TN_CUDA(cudaMemcpy(m.base, buf.data(), buf.size() * sizeof(T), cudaMemcpyHostToDevice));
+  TN_CUDA(cudaMemcpy(m.ranks, ranks, (s->L + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+template <typename T>
+static int create_impl(tnlbm_sim* s) {
+  tnlbm_config& C = s->cfg;
+  TN_CUDA(cudaStreamCreateWithFlags(&s->s0, cudaStreamNonBlocking));
+  TN_CUDA(cudaStreamCreateWithFlags(&s->s1, cudaStreamNonBlocking));
+  TN_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  TN_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+  s->d_scal = (double*)s->arena.alloc(SC_COUNT * sizeof(double));
+  s->d_status = (int*)s->arena.alloc(STATUS_INTS * sizeof(int));
+  if (!s->d_scal || !s->d_status) return TNLBM_E_OOM;
+  cudaMemset(s->d_scal, 0, SC_COUNT * sizeof(double));
+  cudaMemset(s->d_status, 0, STATUS_INTS * sizeof(int));
+  const int Q = s->lat.Q;
+  // state
+  for (int i = 0; i < Q; ++i) {
+    int id = new_node(s, C.chi_max, 0);
+    if (id < 0) return TNLBM_E_OOM;
+    s->f_state.push_back(id);
+  }
+  // mask m_O
+  const size_t ncell = (size_t)s->N * s->N * s->N;
+  if (C.mask_cores || C.solid) {
+    const int mcap = C.mask_cores ? C.mask_cap : std::max(1, C.chi_mask);
+    s->mask_node = new_node(s, mcap, 0);
+    if (s->mask_node < 0) return TNLBM_E_OOM;
+    if (C.mask_cores) {
+      int rc = upload_host_mps<T>(s, s->mask_node, C.mask_cores, C.mask_ranks, C.mask_cap);
+      if (rc) return rc;
+    } else {
+      std::vector<T> h(ncell);
+      for (size_t i = 0; i < ncell; ++i) h[i] = (T)(C.solid[i] ? 1 : 0);
+      T* d = nullptr;
+      TN_CUDA(cudaMalloc(&d, ncell * sizeof(T)));
+      cudaMemcpy(d, h.data(), ncell * sizeof(T), cudaMemcpyHostToDevice);
+      const MpsRef& m = s->nodes[s->mask_node];
+      int rc = tt_svd_dense<T>(d, s->n, (T*)m.base, m.ranks, m.cap, m.cap, C.eps_mask, s->d_status, s->s0);
+      cudaFree(d);
+      if (rc) return rc;
+    }
+    // N_fluid = N^3 - <m_O, 1>
+    MpsRef* dref = (MpsRef*)s->arena.alloc(sizeof(MpsRef));
+    double* dout = (double*)s->arena.alloc(sizeof(double));
+    cudaMemcpy(dref, &s->nodes[s->mask_node], sizeof(MpsRef), cudaMemcpyHostToDevice);
+    launch_inner_ones<T>(dref, 1, s->L, dout, s->s0);
+    double hm = 0.0;
+    cudaMemcpyAsync(&hm, dout, sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+    TN_CUDA(cudaStreamSynchronize(s->s0));
+    s->n_fluid = (double)ncell - hm;
+  } else {
+    s->n_fluid = (double)ncell;
+  }
+  // initial populations
+  {
+    std::vector<RoundJob> jobs(Q);
+    std::vector<int> mode_nodes;
+    if (C.n_modes > 0) {
+      if (C.n_modes + 1 > TN_MAXT) { set_error("n_modes too large"); return TNLBM_E_ARG; }
+      std::vector<std::vector<double>> cores;
+      for (int m = 0; m < C.n_modes; ++m) {
+        int id = new_node(s, 2, 0);
+        if (id < 0) return TNLBM_E_OOM;
+        mode_cores(s->n, C.modes + 8 * m, cores);
+        std::vector<double> flat(mps_size(s->L, 2), 0.0);
+        std::vector<int> rk(s->L + 1, 2);
+        rk[0] = 1; rk[s->L] = 1;
+        for (int k = 0; k < s->L; ++k)
+          std::copy(cores[k].begin(), cores[k].end(), flat.begin() + core_offset(s->L, 2, k));
+        int rc = upload_host_mps<T>(s, id, flat.data(), rk.data(), 2);
+        if (rc) return rc;
+        mode_nodes.push_back(id);
+      }
+    }
+    for (int i = 0; i < Q; ++i) {
+      RoundJob& j = jobs[i];
+      j = RoundJob{};
+      j.chi = C.chi_max; j.eps = C.eps;
+      j.dst = s->nodes[s->f_state[i]];
+      const double w = s->lat.w[i];
+      int t = 0;
+      j.t[t] = Term{}; j.t[t].kind = T_ONES; j.t[t].coef = w; j.t[t].coef_slot = -1; ++t;
+      if (C.n_modes > 0) {
+        for (int m = 0; m < C.n_modes; ++m) {
+          const double* row = C.modes + 8 * m;
+          double cu = 0.0;
+          for (int d = 0; d < 3; ++d) cu += s->lat.c[i][d] * row[5 + d];
+          j.t[t] = Term{}; j.t[t].kind = T_PLAIN; j.t[t].x = s->nodes[mode_nodes[m]];
+          j.t[t].coef = w * (row[4] + 3.0 * cu); j.t[t].coef_slot = -1; ++t;
+        }
+      } else if (s->mask_node >= 0) {
+        j.t[t] = Term{}; j.t[t].kind = T_PLAIN; j.t[t].x = s->nodes[s->mask_node];
+        j.t[t].coef = -w; j.t[t].coef_slot = -1; ++t;
+      }
+      j.nterms = t;
+    }
+    int rc = run_round_now<T>(s, jobs);
+    if (rc) return rc;
+  }
+  // the step DAG
+  Builder b{s};
+  b.build_step();
+  if (b.oom) { set_error("out of device memory building the step"); return TNLBM_E_OOM; }
+  s->d_masks = s->arena.alloc(std::max<size_t>(s->mask_vecs.size(), 2) * sizeof(T));
+  {
+    std::vector<T> mv(std::max<size_t>(s->mask_vecs.size(), 2), (T)0);
+    for (size_t i = 0; i < s->mask_vecs.size(); ++i) mv[i] = (T)s->mask_vecs[i];
+    cudaMemcpy(s->d_masks, mv.data(), mv.size() * sizeof(T), cudaMemcpyHostToDevice);
+  }
+  s->d_rho_ref = (MpsRef*)s->arena.alloc(sizeof(MpsRef));
+  cudaMemcpy(s->d_rho_ref, &s->nodes[s->rho_node], sizeof(MpsRef), cudaMemcpyHostToDevice);
+  {
+    std::vector<MpsRef> src, dst;
+    for (int i = 0; i < Q; ++i) { src.push_back(s->nodes[s->f_next[i]]); dst.push_back(s->nodes[s->f_state[i]]); }
+    s->d_copy_src = (MpsRef*)s->arena.alloc(Q * sizeof(MpsRef));
+    s->d_copy_dst = (MpsRef*)s->arena.alloc(Q * sizeof(MpsRef));
+    cudaMemcpy(s->d_copy_src, src.data(), Q * sizeof(MpsRef), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_copy_dst, dst.data(), Q * sizeof(MpsRef), cudaMemcpyHostToDevice);
+  }
+  int rc = upload_levels<T>(s);
+  if (rc) return rc;
+  // capture one step as a graph
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  TN_CUDA(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  enqueue_step<T>(s, &launches);
+  TN_CUDA(cudaStreamEndCapture(s->s0, &s->graph));
+  TN_CUDA(cudaGraphInstantiate(&s->gexec, s->graph, 0));
+  s->launches_per_step = launches;
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0]) return status_to_code(st);
+  return 0;
+}
+
+}  // namespace tn
+
+// ================================================================ C ABI
+extern "C" {
+
+const char* tnlbm_last_error(void) { return tn::g_err.c_str(); }
+
+size_t tnlbm_mps_size(int L, int cap) { return tn::mps_size(L, cap); }
+size_t tnlbm_mps_offset(int L, int cap, int k) { return tn::core_offset(L, cap, k); }
+
+int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
+  if (!out) { set_error("out is NULL"); return TNLBM_E_ARG; }
+  *out = nullptr;
+  if (!cfg) { set_error("cfg is NULL"); return TNLBM_E_ARG; }
+  const tnlbm_config& C = *cfg;
+  if (C.n_per_axis < 1 || C.n_per_axis > 10) { set_error("n_per_axis must be in [1, 10]"); return TNLBM_E_ARG; }
+  if (C.lattice != TNLBM_D3Q19 && C.lattice != TNLBM_D3Q15) { set_error("lattice must be 19 or 15"); return TNLBM_E_ARG; }
+  if (!(C.tau > 0.5)) { set_error("tau must exceed 0.5"); return TNLBM_E_ARG; }
+  if (C.chi_max < 1 || C.chi_max > 512) { set_error("chi_max must be in [1, 512]"); return TNLBM_E_ARG; }
+  if (C.eps < 0.0) { set_error("eps must be >= 0"); return TNLBM_E_ARG; }
+  if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32) { set_error("bad precision"); return TNLBM_E_ARG; }
+  if (C.hadamard != TNLBM_HADAMARD_FIT && C.hadamard != TNLBM_HADAMARD_EXACT) { set_error("bad hadamard mode"); return TNLBM_E_ARG; }
+  if (C.solid && C.mask_cores) { set_error("give solid voxels or mask cores, not both"); return TNLBM_E_ARG; }
+  if (C.mask_cores && (!C.mask_ranks || C.mask_cap < 1)) { set_error("mask_ranks / mask_cap missing"); return TNLBM_E_ARG; }
+  if (C.solid && (C.chi_mask < 1 || C.chi_mask > 512)) { set_error("chi_mask must be in [1, 512]"); return TNLBM_E_ARG; }
+  if (C.n_modes < 0 || (C.n_modes > 0 && !C.modes)) { set_error("modes missing"); return TNLBM_E_ARG; }
+  tnlbm_sim* s = new (std::nothrow) tnlbm_sim();
+  if (!s) { set_error("host allocation failed"); return TNLBM_E_OOM; }
+  s->n = C.n_per_axis;
+  s->L = 3 * s->n;
+  s->N = 1 << s->n;
+  s->prec = C.precision;
+  s->esz = C.precision == TNLBM_FP64 ? 8 : 4;
+  s->lat = make_lattice(C.lattice);
+  s->cfg = C;              // pointers are used during create only
+  if (s->cfg.sweeps <= 0) s->cfg.sweeps = 2;
+  int rc = C.precision == TNLBM_FP64 ? tn::create_impl<double>(s) : tn::create_impl<float>(s);
+  s->cfg.solid = nullptr;
+  s->cfg.mask_cores = nullptr;
+  s->cfg.mask_ranks = nullptr;
+  s->cfg.modes = nullptr;
+  if (rc) {
+    std::string msg = tn::g_err;
+    tnlbm_destroy(s);
+    tn::g_err = msg;
+    return rc;
+  }
+  *out = s;
+  return 0;
+}
+
+int tnlbm_step(tnlbm_sim* s, int k) {
+  if (!s || k < 0) { set_error("bad arguments to tnlbm_step"); return TNLBM_E_ARG; }
+  for (int i = 0; i < k; ++i) TN_CUDA(cudaGraphLaunch(s->gexec, s->s0));
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  s->steps += k;
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0]) {
+    int rc = status_to_code(st);
+    cudaMemset(s->d_status, 0, STATUS_INTS * sizeof(int));
+    return rc;
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int macro_impl(tnlbm_sim* s, double* rho, double* u) {
+  using namespace tn;
+  const size_t nc = (size_t)s->N * s->N * s->N;
+  double *d = nullptr, *dm = nullptr;
+  T* tmp = nullptr;
+  void* scr = nullptr;
+  const int capmax = std::max(s->cfg.chi_max, s->mask_node >= 0 ? s->nodes[s->mask_node].cap : 1);
+  const size_t sb = contract_scratch_bytes(s->n, capmax, sizeof(T));
+  auto fin = [&](int rc) { cudaFree(d); cudaFree(dm); cudaFree(tmp); cudaFree(scr); return rc; };
+  if (cudaMalloc(&d, 4 * nc * sizeof(double)) != cudaSuccess || cudaMalloc(&tmp, nc * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&scr, sb) != cudaSuccess) {
+    set_error("out of device memory in tnlbm_macroscopic");
+    return fin(TNLBM_E_OOM);
+  }
+  double *dr = d, *jx = d + nc, *jy = d + 2 * nc, *jz = d + 3 * nc;
+  for (int i = 0; i < s->lat.Q; ++i) {
+    contract_dense<T>(s->nodes[s->f_state[i]], s->n, tmp, scr, sb, s->s0);
+    launch_accum_moments<T>(tmp, nc, dr, jx, jy, jz, s->lat.c[i][0], s->lat.c[i][1], s->lat.c[i][2], i == 0, s->s0);
+  }
+  if (s->mask_node >= 0) {
+    if (cudaMalloc(&dm, nc * sizeof(double)) != cudaSuccess) return fin(TNLBM_E_OOM);
+    contract_dense<T>(s->nodes[s->mask_node], s->n, tmp, scr, sb, s->s0);
+    launch_cast_double<T>(tmp, nc, dm, s->s0);
+  }
+  if (u) launch_velocity(nc, dr, jx, jy, jz, dm, s->cfg.force[0], s->cfg.force[1], s->cfg.force[2], s->s0);
+  if (rho) cudaMemcpyAsync(rho, dr, nc * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+  if (u) cudaMemcpyAsync(u, jx, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+  cudaError_t e = cudaStreamSynchronize(s->s0);
+  if (e != cudaSuccess) return fin(cuda_fail(e, "tnlbm_macroscopic"));
+  return fin(0);
+}
+
+template <typename T>
+static int get_pop_impl(tnlbm_sim* s, double* cores, int* ranks) {
+  using namespace tn;
+  const size_t ms = mps_size(s->L, s->cfg.chi_max);
+  std::vector<T> buf(ms);
+  for (int i = 0; i < s->lat.Q; ++i) {
+    const MpsRef& m = s->nodes[s->f_state[i]];
+    TN_CUDA(cudaMemcpy(buf.data(), m.base, ms * sizeof(T), cudaMemcpyDeviceToHost));
+    if (cores) for (size_t e = 0; e < ms; ++e) cores[(size_t)i * ms + e] = (double)buf[e];
+    if (ranks) TN_CUDA(cudaMemcpy(ranks + (size_t)i * (s->L + 1), m.ranks, (s->L + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  return 0;
+}
+
+template <typename T>
+static int set_pop_impl(tnlbm_sim* s, const double* cores, const int* ranks) {
+  using namespace tn;
+  const size_t ms = mps_size(s->L, s->cfg.chi_max);
+  for (int i = 0; i < s->lat.Q; ++i) {
+    int rc = upload_host_mps<T>(s, s->f_state[i], cores + (size_t)i * ms, ranks + (size_t)i * (s->L + 1), s->cfg.chi_max);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+extern "C" {
+
+int tnlbm_macroscopic(tnlbm_sim* s, double* rho, double* u) {
+  if (!s) { set_error("sim is NULL"); return TNLBM_E_ARG; }
+  return s->prec == TNLBM_FP64 ? macro_impl<double>(s, rho, u) : macro_impl<float>(s, rho, u);
+}
+
+int tnlbm_get_populations(tnlbm_sim* s, double* cores, int* ranks) {
+  if (!s) { set_error("sim is NULL"); return TNLBM_E_ARG; }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  return s->prec == TNLBM_FP64 ? get_pop_impl<double>(s, cores, ranks) : get_pop_impl<float>(s, cores, ranks);
+}
+
+int tnlbm_set_populations(tnlbm_sim* s, const double* cores, const int* ranks) {
+  if (!s || !cores || !ranks) { set_error("NULL argument"); return TNLBM_E_ARG; }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  return s->prec == TNLBM_FP64 ? set_pop_impl<double>(s, cores, ranks) : set_pop_impl<float>(s, cores, ranks);
+}
+
+int tnlbm_stats_get(tnlbm_sim* s, tnlbm_stats* out) {
+  if (!s || !out) { set_error("NULL argument"); return TNLBM_E_ARG; }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  std::vector<int> rk((size_t)s->lat.Q * (s->L + 1));
+  for (int i = 0; i < s->lat.Q; ++i)
+    TN_CUDA(cudaMemcpy(rk.data() + (size_t)i * (s->L + 1), s->nodes[s->f_state[i]].ranks, (s->L + 1) * sizeof(int),
+                       cudaMemcpyDeviceToHost));
+  int mx = 0;
+  double sum = 0.0, nv = 0.0;
+  int cnt = 0;
+  for (int i = 0; i < s->lat.Q; ++i)
+    for (int k = 0; k <= s->L; ++k) {
+      int r = rk[(size_t)i * (s->L + 1) + k];
+      mx = std::max(mx, r);
+      if (k > 0 && k < s->L) { sum += r; ++cnt; }
+      if (k < s->L) nv += (double)r * 2.0 * rk[(size_t)i * (s->L + 1) + k + 1];
+    }
+  double scal[SC_COUNT] = {0};
+  TN_CUDA(cudaMemcpy(scal, s->d_scal, sizeof(scal), cudaMemcpyDeviceToHost));
+  int st = 0;
+  TN_CUDA(cudaMemcpy(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  out->steps = s->steps;
+  out->max_bond = mx;
+  out->mean_bond = cnt ? sum / cnt : 0.0;
+  out->nvps = nv;
+  out->compression_ratio = nv > 0 ? (double)s->lat.Q * s->N * s->N * s->N / nv : 0.0;
+  out->rho0 = scal[SC_RHO0];
+  out->status = st;
+  out->gpu_launches_per_step = s->launches_per_step;
+  return 0;
+}
+
+int tnlbm_destroy(tnlbm_sim* s) {
+  if (!s) return 0;
+  if (s->s0) cudaStreamSynchronize(s->s0);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->s0) cudaStreamDestroy(s->s0);
+  if (s->s1) cudaStreamDestroy(s->s1);
+  delete s;
+  return 0;
+}
+
+}  // extern "C"
+
+// ================================================================ primitives
+namespace tn {
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+  bool alloc(size_t b) { return cudaMalloc(&p, b ? b : 16) == cudaSuccess; }
+};
+
+static int check_status(int* d_status, cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "primitive");
+  int h[STATUS_INTS] = {0};
+  e = cudaMemcpy(h, d_status, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  return status_to_code(h);
+}
+
+template <typename T>
+static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* terms, void* const* dst,
+                        int* const* dst_ranks, int dst_cap, int chi, double eps, int materialize,
+                        cudaStream_t st) {
+  const int L = 3 * n_bits;
+  std::vector<RoundJob> jobs(batch);
+  std::vector<T> masks;
+  for (int b = 0; b < batch; ++b) {
+    RoundJob& j = jobs[b];
+    j = RoundJob{};
+    j.nterms = nterms;
+    j.chi = chi;
+    j.eps = eps;
+    j.materialize_only = materialize;
+    j.dst.base = dst[b];
+    j.dst.ranks = dst_ranks[b];
+    j.dst.cap = dst_cap;
+    for (int t = 0; t < nterms; ++t) {
+      const tnlbm_term& in = terms[(size_t)b * nterms + t];
+      Term& tm = j.t[t];
+      tm = Term{};
+      tm.kind = in.kind;
+      tm.coef = in.coef;
+      tm.coef_slot = -1;
+      tm.axis = in.axis;
+      tm.offset = in.offset;
+      tm.cyclic = in.cyclic;
+      tm.mask_id = -1;
+      if (in.kind < 0 || in.kind > 4) { set_error("bad term kind"); return TNLBM_E_ARG; }
+      if (in.kind != T_ONES) {
+        if (!in.x || !in.x_ranks || in.x_cap < 1) { set_error("term operand missing"); return TNLBM_E_ARG; }
+        tm.x.base = (void*)in.x; tm.x.ranks = (int*)in.x_ranks; tm.x.cap = in.x_cap;
+      }
+      if (in.kind == T_KRON) {
+        if (!in.y || !in.y_ranks || in.y_cap < 1) { set_error("KRON needs y"); return TNLBM_E_ARG; }
+        tm.y.base = (void*)in.y; tm.y.ranks = (int*)in.y_ranks; tm.y.cap = in.y_cap;
+      }
+      if (in.kind == T_SHIFT && (in.axis < 0 || in.axis > 2 || (in.offset != 1 && in.offset != -1))) {
+        set_error("SHIFT needs axis in 0..2 and offset +-1");
+        return TNLBM_E_ARG;
+      }
+      if (in.kind == T_MASK1) {
+        if (!in.mask) { set_error("MASK1 needs mask vectors"); return TNLBM_E_ARG; }
+        tm.mask_id = (int)(masks.size() / (TN_MAXL * 2));
+        masks.resize(masks.size() + TN_MAXL * 2, (T)1);
+        for (int k = 0; k < L; ++k)
+          for (int s2 = 0; s2 < 2; ++s2) masks[(size_t)tm.mask_id * TN_MAXL * 2 + 2 * k + s2] = (T)in.mask[2 * k + s2];
+      }
+    }
+    plan_round_job(j, L, n_bits, sizeof(T));
+  }
+  size_t tot = 0;
+  for (auto& j : jobs) tot += j.lay.total;
+  DevBuf scr, dj, dm, ds, dsc;
+  if (!scr.alloc(tot * sizeof(T)) || !dj.alloc(batch * sizeof(RoundJob)) ||
+      !dm.alloc(std::max<size_t>(masks.size(), 2) * sizeof(T)) || !ds.alloc(STATUS_INTS * sizeof(int)) ||
+      !dsc.alloc(SC_COUNT * sizeof(double))) {
+    set_error("out of device memory");
+    return TNLBM_E_OOM;
+  }
+  size_t o = 0;
+  for (auto& j : jobs) { j.scratch = (T*)scr.p + o; o += j.lay.total; }
+  TN_CUDA(cudaMemcpyAsync(dj.p, jobs.data(), batch * sizeof(RoundJob), cudaMemcpyHostToDevice, st));
+  if (!masks.empty()) TN_CUDA(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
+  TN_CUDA(cudaMemsetAsync(dsc.p, 0, SC_COUNT * sizeof(double), st));
+  launch_round<T>((const RoundJob*)dj.p, batch, L, n_bits, (const T*)dm.p, (const double*)dsc.p, (int*)ds.p, st);
+  TN_CUDA(cudaGetLastError());
+  return check_status((int*)ds.p, st);
+}
+
+template <typename T>
+static int fit_impl(int n_bits, int batch, const void* const* B, const int* const* rB, int capB,
+                    const void* const* C, const int* const* rC, int capC, void* const* A,
+                    int* const* rA, int capA, int sweeps, cudaStream_t st) {
+  const int L = 3 * n_bits;
+  std::vector<FitJob> jobs(batch);
+  size_t tot = 0;
+  for (int b = 0; b < batch; ++b) {
+    FitJob& j = jobs[b];
+    j = FitJob{};
+    j.A.base = A[b]; j.A.ranks = rA[b]; j.A.cap = capA;
+    j.B.base = (void*)B[b]; j.B.ranks = (int*)rB[b]; j.B.cap = capB;
+    j.C.base = (void*)C[b]; j.C.ranks = (int*)rC[b]; j.C.cap = capC;
+    size_t env, xs, ys, ab, q;
+    plan_fit_job(j, L, &env, &xs, &ys, &ab, &q);
+    j.env_stride = env;
+    j.qscr_stride = q;
+    tot += 2 * (L + 1) * env + xs + ys + ab + 4 * q;
+  }
+  DevBuf scr, dj, ds;
+  if (!scr.alloc(tot * sizeof(T)) || !dj.alloc(batch * sizeof(FitJob)) || !ds.alloc(STATUS_INTS * sizeof(int))) {
+    set_error("out of device memory");
+    return TNLBM_E_OOM;
+  }
+  size_t o = 0;
+  for (auto& j : jobs) {
+    T* base = (T*)scr.p;
+    size_t env, xs, ys, ab, q;
+    plan_fit_job(j, L, &env, &xs, &ys, &ab, &q);
+    j.env_l = base + o; o += (L + 1) * env;
+    j.env_r = base + o; o += (L + 1) * env;
+    j.x = base + o; o += xs;
+    j.y = base + o; o += ys;
+    j.abuf = base + o; o += ab;
+    j.qscr = base + o; o += 4 * q;
+  }
+  TN_CUDA(cudaMemcpyAsync(dj.p, jobs.data(), batch * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+  TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
+  run_fit<T>((const FitJob*)dj.p, jobs, L, sweeps, (int*)ds.p, st);
+  TN_CUDA(cudaGetLastError());
+  return check_status((int*)ds.p, st);
+}
+
+}  // namespace tn
+
+extern "C" {
+
+int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const tnlbm_term* terms,
+                        void* const* dst, int* const* dst_ranks, int dst_cap, int chi_max, double eps,
+                        void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || nterms < 1 || nterms > TN_MAXT || !terms || !dst ||
+      !dst_ranks || chi_max < 1 || chi_max > dst_cap || chi_max > 512 || eps < 0) {
+    set_error("bad arguments to tnlbm_lincomb_round");
+    return TNLBM_E_ARG;
+  }
+  if (batch == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  return precision == TNLBM_FP64
+             ? tn::lincomb_impl<double>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st)
+             : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st);
+}
+
+int tnlbm_materialize(int precision, int n_bits, int batch, const tnlbm_term* terms, void* const* dst,
+                      int* const* dst_ranks, int dst_cap, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || !terms || !dst || !dst_ranks || dst_cap < 1) {
+    set_error("bad arguments to tnlbm_materialize");
+    return TNLBM_E_ARG;
+  }
+  if (batch == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  return precision == TNLBM_FP64
+             ? tn::lincomb_impl<double>(n_bits, batch, 1, terms, dst, dst_ranks, dst_cap, 1, 0.0, 1, st)
+             : tn::lincomb_impl<float>(n_bits, batch, 1, terms, dst, dst_ranks, dst_cap, 1, 0.0, 1, st);
+}
+
+int tnlbm_hadamard_fit(int precision, int n_bits, int batch, const void* const* B, const int* const* rB,
+                       int capB, const void* const* C, const int* const* rC, int capC, void* const* A,
+                       int* const* rA, int capA, int sweeps, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || !B || !rB || !C || !rC || !A || !rA || capA < capB ||
+      capB < 1 || capC < 1 || sweeps < 1 || capA > 1024 || capB * 2 > 1024) {
+    set_error("bad arguments to tnlbm_hadamard_fit");
+    return TNLBM_E_ARG;
+  }
+  if (batch == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  return precision == TNLBM_FP64
+             ? tn::fit_impl<double>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st)
+             : tn::fit_impl<float>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st);
+}
+
+int tnlbm_inner_ones(int precision, int n_bits, int batch, const void* const* X, const int* const* rX,
+                     int capX, double* out, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || !X || !rX || !out || capX < 1 || capX > 1024) {
+    set_error("bad arguments to tnlbm_inner_ones");
+    return TNLBM_E_ARG;
+  }
+  if (batch == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<tn::MpsRef> refs(batch);
+  for (int b = 0; b < batch; ++b) { refs[b].base = (void*)X[b]; refs[b].ranks = (int*)rX[b]; refs[b].cap = capX; }
+  tn::DevBuf d;
+  if (!d.alloc(batch * sizeof(tn::MpsRef))) { set_error("out of device memory"); return TNLBM_E_OOM; }
+  TN_CUDA(cudaMemcpyAsync(d.p, refs.data(), batch * sizeof(tn::MpsRef), cudaMemcpyHostToDevice, st));
+  if (precision == TNLBM_FP64) tn::launch_inner_ones<double>((const tn::MpsRef*)d.p, batch, 3 * n_bits, out, st);
+  else tn::launch_inner_ones<float>((const tn::MpsRef*)d.p, batch, 3 * n_bits, out, st);
+  TN_CUDA(cudaGetLastError());
+  TN_CUDA(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int tnlbm_to_dense(int precision, int n_bits, const void* X, const int* rX, int capX, void* dense, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || !X || !rX || !dense || capX < 1 || capX > 1024) {
+    set_error("bad arguments to tnlbm_to_dense");
+    return TNLBM_E_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  tn::MpsRef m{(void*)X, (int*)rX, capX};
+  const size_t es = precision == TNLBM_FP64 ? 8 : 4;
+  const size_t sb = tn::contract_scratch_bytes(n_bits, capX, es);
+  tn::DevBuf scr;
+  if (!scr.alloc(sb)) { set_error("out of device memory"); return TNLBM_E_OOM; }
+  int rc = precision == TNLBM_FP64 ? tn::contract_dense<double>(m, n_bits, (double*)dense, scr.p, sb, st)
+                                   : tn::contract_dense<float>(m, n_bits, (float*)dense, scr.p, sb, st);
+  if (rc) return rc;
+  TN_CUDA(cudaGetLastError());
+  TN_CUDA(cudaStreamSynchronize(st));
+  return 0;
+}
+
+int tnlbm_from_dense(int precision, int n_bits, const void* dense, void* dst, int* dst_ranks, int dst_cap,
+                     int chi_max, double eps, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || !dense || !dst || !dst_ranks || dst_cap < 1 || chi_max < 1 ||
+      chi_max > dst_cap || 2 * chi_max > 1024 || eps < 0) {
+    set_error("bad arguments to tnlbm_from_dense");
+    return TNLBM_E_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  tn::DevBuf ds;
+  if (!ds.alloc(STATUS_INTS * sizeof(int))) { set_error("out of device memory"); return TNLBM_E_OOM; }
+  TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
+  int rc = precision == TNLBM_FP64
+               ? tn::tt_svd_dense<double>((const double*)dense, n_bits, (double*)dst, dst_ranks, dst_cap, chi_max, eps, (int*)ds.p, st)
+               : tn::tt_svd_dense<float>((const float*)dense, n_bits, (float*)dst, dst_ranks, dst_cap, chi_max, eps, (int*)ds.p, st);
+  if (rc) return rc;
+  return tn::check_status((int*)ds.p, st);
+}
+
+}  // extern "C"
+
+// ================================================================ measurement
+template <typename T>
+static int profile_impl(tnlbm_sim* s, double* ms, double* flops, int* launches) {
+  using namespace tn;
+  double* d_ctr = nullptr;
+  TN_CUDA(cudaMalloc(&d_ctr, C_COUNT * sizeof(double)));
+  cudaMemsetAsync(d_ctr, 0, C_COUNT * sizeof(double), s->s0);
+  Prof prof;
+  prof.st = s->s0;
+  prof.d_ctr = d_ctr;
+  prof.begin();
+  int n = 0;
+  enqueue_step<T>(s, &n, &prof);
+  cudaError_t e = cudaStreamSynchronize(s->s0);
+  if (e != cudaSuccess) { cudaFree(d_ctr); return cuda_fail(e, "tnlbm_profile_step"); }
+  for (int c = 0; c < C_COUNT; ++c) { ms[c] = 0.0; launches[c] = 0; }
+  prof.collect(ms, launches);
+  cudaMemcpy(flops, d_ctr, C_COUNT * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_ctr);
+  s->steps += 1;
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0]) { cudaMemset(s->d_status, 0, sizeof(st)); return status_to_code(st); }
+  return 0;
+}
+
+extern "C" {
+
+int tnlbm_step_timed(tnlbm_sim* s, int k, double* ms) {
+  if (!s || k < 0 || !ms) { set_error("bad arguments to tnlbm_step_timed"); return TNLBM_E_ARG; }
+  cudaEvent_t a, b;
+  TN_CUDA(cudaEventCreate(&a));
+  TN_CUDA(cudaEventCreate(&b));
+  TN_CUDA(cudaEventRecord(a, s->s0));
+  for (int i = 0; i < k; ++i) TN_CUDA(cudaGraphLaunch(s->gexec, s->s0));
+  TN_CUDA(cudaEventRecord(b, s->s0));
+  TN_CUDA(cudaEventSynchronize(b));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = t;
+  s->steps += k;
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0]) { cudaMemset(s->d_status, 0, sizeof(st)); return status_to_code(st); }
+  return 0;
+}
+
+int tnlbm_profile_step(tnlbm_sim* s, double* ms, double* flops, int* launches) {
+  if (!s || !ms || !flops || !launches) { set_error("bad arguments to tnlbm_profile_step"); return TNLBM_E_ARG; }
+  return s->prec == TNLBM_FP64 ? profile_impl<double>(s, ms, flops, launches)
+                               : profile_impl<float>(s, ms, flops, launches);
+}
+
+}  // extern "C"

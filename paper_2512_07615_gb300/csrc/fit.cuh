@@ -1,0 +1,95 @@
+// Product-fit jobs (Sec. 2.3) and the other batched kernels' launchers.
+#pragma once
+
+#include "internal.cuh"
+
+namespace tn {
+
+struct FitJob {
+  MpsRef A, B, C;          // A: candidate and output (set to B first)
+  void* env_l;             // T*, (L+1) left environments, stride env_stride
+  void* env_r;             // T*, (L+1) right environments
+  size_t env_stride;
+  void* x;                 // intermediates of the local contraction
+  void* y;
+  void* abuf;              // new centre core before the QR / LQ shift
+  void* qscr;              // 4 * qscr_stride elements of QR scratch
+  size_t qscr_stride;
+};
+
+void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* y_elems,
+                  size_t* abuf_elems, size_t* q_elems);
+
+// Eager-launch profiler: an event after every launch on one stream; the time
+// between consecutive events is charged to the class of the launch.
+struct Prof {
+  cudaStream_t st = nullptr;
+  double* d_ctr = nullptr;            // device FLOP counters [C_COUNT]
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+  void begin() { cudaEventCreate(&start); cudaEventRecord(start, st); }
+  void mark(int c) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    cudaEventRecord(e, st);
+    ev.push_back(e);
+    cls.push_back(c);
+  }
+  // ms[c], launches[c]; destroys the events
+  void collect(double* ms, int* launches) {
+    cudaEventSynchronize(ev.empty() ? start : ev.back());
+    cudaEvent_t prev = start;
+    for (size_t i = 0; i < ev.size(); ++i) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, prev, ev[i]);
+      ms[cls[i]] += t;
+      launches[cls[i]] += 1;
+      prev = ev[i];
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(start);
+    ev.clear();
+    cls.clear();
+  }
+};
+
+template <typename T>
+int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int sweeps, int* d_status,
+            cudaStream_t st, Prof* prof = nullptr);
+
+// ---- misc.cu
+// out[b] = <X_b, 1> for MPS refs in device memory
+template <typename T>
+void launch_inner_ones(const MpsRef* d_refs, int n, int L, double* d_out, cudaStream_t st);
+
+// rho_0 = <rho,1> / n_fluid and the scalar slots used by the Taylor 1/rho terms
+enum ScalSlot : int { SC_NEG_RHO0 = 0, SC_INV1 = 1, SC_INV2 = 2, SC_INV3 = 3, SC_RHO0 = 4, SC_COUNT = 8 };
+template <typename T>
+void launch_rho0(const MpsRef* d_rho, int L, double n_fluid, double* d_scal, cudaStream_t st);
+
+// copy MPS src[b] -> dst[b] (cores and bonds)
+template <typename T>
+void launch_copy(const MpsRef* d_src, const MpsRef* d_dst, int n, int L, cudaStream_t st);
+
+// dense[x][y][z] = contraction of X (host-known ranks not needed)
+template <typename T>
+int contract_dense(const MpsRef& X, int n_bits, T* d_dense, void* d_scratch, size_t scratch_bytes,
+                   cudaStream_t st);
+size_t contract_scratch_bytes(int n_bits, int cap, size_t elem);
+
+// accumulate rho += f, j += c f (double) from a dense population
+template <typename T>
+void launch_accum_moments(const T* d_f, size_t ncell, double* rho, double* jx, double* jy,
+                          double* jz, int cx, int cy, int cz, int first, cudaStream_t st);
+template <typename T>
+void launch_cast_double(const T* src, size_t n, double* dst, cudaStream_t st);
+void launch_velocity(size_t ncell, const double* rho, double* jx, double* jy, double* jz,
+                     const double* mask, double fx, double fy, double fz, cudaStream_t st);
+
+// TT-SVD of a dense device field (FP64 Gram matrices); host-synchronous.
+template <typename T>
+int tt_svd_dense(const T* d_dense_xyz, int n_bits, T* d_dst, int* d_dst_ranks, int dst_cap,
+                 int chi_max, double eps, int* d_status, cudaStream_t st);
+
+}  // namespace tn

@@ -1,0 +1,136 @@
+// Internal declarations of libtnlbm: flat MPS layout, rounding/fit job
+// descriptors, status codes and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tnlbm.h"
+
+#define TN_MAXL 32     // sites per MPS (n_bits <= 10 -> L <= 30)
+#define TN_MAXT 40     // terms per rounding job
+
+namespace tn {
+
+// ------------------------------------------------------------ status word
+// Kernels never trap: they record a code in a device status word and return.
+enum : int {
+  ST_OK = 0,
+  ST_CAPACITY = 1,   // a realised bond exceeded a buffer capacity
+  ST_NOCONV = 2,     // Jacobi sweep limit reached
+  ST_NAN = 4,        // non-finite value seen
+  ST_TIMEOUT = 8     // bounded wait ran out
+};
+// algorithmic FLOP counters per kernel class (profiling only; nullable)
+enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 = 4, C_COPY = 5, C_COUNT = 6 };
+// Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
+__host__ __device__ inline double qr_flops(double m, double n) {
+  const double k = m < n ? m : n, big = m < n ? n : m;
+  return 4.0 * big * k * k - 4.0 / 3.0 * k * k * k;
+}
+// thin SVD with both singular-vector sets (Golub-Kahan-Reinsch count)
+__host__ __device__ inline double svd_flops(double m, double n) {
+  const double k = m < n ? m : n, big = m < n ? n : m;
+  return 4.0 * big * k * k + 8.0 * k * k * k;
+}
+// status buffers hold STATUS_INTS ints: [0] flags, [1] diag taken, [2..5] where
+static constexpr int STATUS_INTS = 8;
+
+__host__ __device__ inline int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int imax(int a, int b) { return a > b ? a : b; }
+
+// bond capacity of a flat MPS: 1 at the two ends, cap inside (exactly formed
+// sums, products and MPO applications may exceed 2^k near the ends)
+__host__ __device__ inline int bond_cap(int L, int cap, int k) {
+  return (k == 0 || k == L) ? 1 : cap;
+}
+
+__host__ __device__ inline size_t core_offset(int L, int cap, int k) {
+  size_t off = 0;
+  for (int j = 0; j < k; ++j)
+    off += (size_t)bond_cap(L, cap, j) * 2 * (size_t)bond_cap(L, cap, j + 1);
+  return off;
+}
+
+__host__ __device__ inline size_t mps_size(int L, int cap) { return core_offset(L, cap, L); }
+
+// A device MPS in the flat layout.
+struct MpsRef {
+  void* base;      // T*
+  int* ranks;      // [L+1]
+  int cap;
+};
+
+// ------------------------------------------------------------ rounding jobs
+enum TermKind : int { T_PLAIN = 0, T_SHIFT = 1, T_MASK1 = 2, T_KRON = 3, T_ONES = 4 };
+
+struct Term {
+  int kind;
+  int axis, offset, cyclic;   // SHIFT
+  double coef;
+  int coef_slot;              // -1, or index of a device scalar multiplying coef
+  int mask_id;                // MASK1: index into the job table's mask vectors
+  MpsRef x, y;
+};
+
+// Scratch partition of one rounding job (elements of T), same on host and device.
+struct RoundLayout {
+  size_t q_off[TN_MAXL + 1];  // left-orthogonal cores of the QR sweep
+  size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, total;
+};
+
+struct RoundJob {
+  int nterms;
+  int chi;
+  double eps;
+  Term t[TN_MAXT];
+  MpsRef dst;
+  void* scratch;              // T*, RoundLayout::total elements
+  int rw[TN_MAXL + 1];        // upper bounds of the wide (summed) bonds
+  int qb[TN_MAXL + 1];        // upper bounds of the QR-sweep bonds
+  RoundLayout lay;
+  int materialize_only;       // 1: write the (single) term to dst, no rounding
+};
+
+// bound of one term's bond k from the capacities of its operands
+__host__ __device__ inline int term_bond_bound(const Term& t, int L, int n_bits, int k) {
+  switch (t.kind) {
+    case T_ONES: return 1;
+    case T_PLAIN:
+    case T_MASK1: return bond_cap(L, t.x.cap, k);
+    case T_KRON: return bond_cap(L, t.x.cap, k) * bond_cap(L, t.y.cap, k);
+    case T_SHIFT: {
+      int first = t.axis, last = t.axis + 3 * (n_bits - 1);
+      int w = (k > first && k <= last) ? 2 : 1;
+      return w * bond_cap(L, t.x.cap, k);
+    }
+  }
+  return 0;
+}
+
+// Fill rw/qb bounds and the scratch layout of a job (host side).
+void plan_round_job(RoundJob& j, int L, int n_bits, size_t elem_bytes);
+
+// ------------------------------------------------------------ error helpers
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define TN_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return ::tn::cuda_fail(_e, #call); \
+  } while (0)
+
+// ------------------------------------------------------------ launchers
+// Rounding / materialisation of `njobs` jobs already resident on the device.
+template <typename T>
+void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits,
+                  const T* d_masks, const double* d_scal, int* d_status,
+                  cudaStream_t st, double* d_ctr = nullptr);
+size_t round_smem_bytes();
+
+}  // namespace tn

@@ -1,0 +1,429 @@
+// In-CTA dense linear algebra used by the rounding sweep and the product fit:
+// block reductions, Householder QR with an explicit Q, and a one-sided
+// (Hestenes) Jacobi SVD.  Matrices are row-major with a leading dimension and
+// may live in shared or global memory (generic pointers).  Every function is
+// called by all threads of the block and ends with __syncthreads().
+#pragma once
+
+#include "internal.cuh"
+
+namespace tn {
+
+template <typename T> struct Eps;
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+template <> struct Eps<float> { static constexpr double v = 1.1920928955078125e-07; };
+
+// sum over the block in type V; `red` is shared scratch of >= 32 V
+template <typename V>
+__device__ inline V block_sum_t(V v, V* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  V s = (V)0;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+    s = lane < nw ? red[lane] : (V)0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// sum over the block; `red` is shared scratch of >= 32 doubles
+__device__ inline double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (wid == 0) {
+    s = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// Householder QR of A (m x n, leading dim lda), in place: on return the upper
+// triangle holds R and the strict lower part the reflector tails.  tau[k],
+// k = min(m, n), receives the reflector scalars (H = I - tau v v^T, v_0 = 1).
+// Then Q (m x k, ld = k) is formed explicitly and R (k x n, ld = n) is copied
+// out with rows sign-normalised so that diag(R) >= 0.
+template <typename T>
+__device__ void householder_qr(T* A, int m, int n, int lda, T* Q, T* R, double* tau,
+                               double* red) {
+  const int kk = imin(m, n);
+  for (int j = 0; j < kk; ++j) {
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+      double v = (double)A[(size_t)i * lda + j];
+      part += v * v;
+    }
+    double sig2 = block_sum(part, red);
+    __shared__ double s_scale;
+    if (threadIdx.x == 0) {
+      double alpha = (double)A[(size_t)j * lda + j];
+      if (sig2 == 0.0) {
+        tau[j] = 0.0;
+        s_scale = 0.0;
+      } else {
+        double beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
+        tau[j] = (beta - alpha) / beta;
+        s_scale = 1.0 / (alpha - beta);
+        A[(size_t)j * lda + j] = (T)beta;
+      }
+    }
+    __syncthreads();
+    const double tj = tau[j];
+    if (tj != 0.0) {
+      const double sc = s_scale;
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
+        A[(size_t)i * lda + j] = (T)((double)A[(size_t)i * lda + j] * sc);
+      __syncthreads();
+      for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
+        T w = A[(size_t)j * lda + c];
+        for (int i = j + 1; i < m; ++i) w += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
+        w *= (T)tj;
+        A[(size_t)j * lda + c] -= w;
+        for (int i = j + 1; i < m; ++i) A[(size_t)i * lda + c] -= w * A[(size_t)i * lda + j];
+      }
+    }
+    __syncthreads();
+  }
+  // R with non-negative diagonal; remember the signs in tau's sign? keep separate
+  for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
+    int i = idx / n, c = idx % n;
+    T d = A[(size_t)i * lda + i] < (T)0 ? (T)-1 : (T)1;
+    R[(size_t)i * n + c] = c >= i ? d * A[(size_t)i * lda + c] : (T)0;
+  }
+  // Q = H_0 ... H_{kk-1} [I; 0], accumulated backwards
+  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+    int i = idx / kk, c = idx % kk;
+    Q[idx] = (i == c) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int j = kk - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj != 0.0) {
+      for (int c = j + threadIdx.x; c < kk; c += blockDim.x) {
+        T w = Q[(size_t)j * kk + c];
+        for (int i = j + 1; i < m; ++i) w += A[(size_t)i * lda + j] * Q[(size_t)i * kk + c];
+        w *= (T)tj;
+        Q[(size_t)j * kk + c] -= w;
+        for (int i = j + 1; i < m; ++i) Q[(size_t)i * kk + c] -= w * A[(size_t)i * lda + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+    int c = idx % kk;
+    if (A[(size_t)c * lda + c] < (T)0) Q[idx] = -Q[idx];
+  }
+  __syncthreads();
+}
+
+// One-sided Jacobi on ncol columns of length len, stored column-contiguous
+// (Wm[j*len + i]); V (ncol x ncol, V[j*ncol + i] = column j) accumulates the
+// rotations.  Parallel ordering: a round-robin tournament, one warp per pair.
+// Returns the number of sweeps used (maxsw + 1 if not converged).
+template <typename T>
+__device__ int jacobi_cols(T* Wm, T* V, int ncol, int len, int maxsw) {
+  for (int idx = threadIdx.x; idx < ncol * ncol; idx += blockDim.x)
+    V[idx] = (idx / ncol == idx % ncol) ? (T)1 : (T)0;
+  __shared__ int s_rot;
+  __syncthreads();
+  if (ncol < 2) return 0;
+  const int np = (ncol + 1) & ~1;          // padded to even; index np-1 may be a dummy
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // stopping threshold on |cos| of a pair: a few ulps above the round-off of a
+  // freshly rotated pair, so short columns cannot cycle on noise
+  const double tol = 16.0 * Eps<T>::v * sqrt((double)len);
+  int sweep = 0;
+  for (; sweep < maxsw; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int p = wid; p < np / 2; p += nw) {
+        int a, b;
+        if (p == 0) { a = rnd; b = np - 1; }
+        else { a = (rnd + p) % (np - 1); b = (rnd - p + (np - 1)) % (np - 1); }
+        if (a >= ncol || b >= ncol) continue;
+        if (a > b) { int t = a; a = b; b = t; }
+        T* wa = Wm + (size_t)a * len;
+        T* wb = Wm + (size_t)b * len;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < len; i += 32) {
+          double x = (double)wa[i], y = (double)wb[i];
+          al += x * x; be += y * y; ga += x * y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        // pairs below the representable range carry nothing; skip them too
+        if (ga == 0.0 || al < 1e-250 || be < 1e-250 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        // Rutishauser's rotation zeroing the (a, b) inner product
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        const T cc = (T)c, ss = (T)s;
+        for (int i = lane; i < len; i += 32) {
+          T x = wa[i], y = wb[i];
+          wa[i] = cc * x - ss * y;
+          wb[i] = ss * x + cc * y;
+        }
+        T* va = V + (size_t)a * ncol;
+        T* vb = V + (size_t)b * ncol;
+        for (int i = lane; i < ncol; i += 32) {
+          T x = va[i], y = vb[i];
+          va[i] = cc * x - ss * y;
+          vb[i] = ss * x + cc * y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+}  // namespace tn
+
+namespace tn {
+
+// ---------------------------------------------------------------- fast in-CTA kernels
+// Designed for 1024-thread CTAs with the working matrix in shared memory.
+
+// C (M x N, ldc) = [C +] A (M x K, lda) * B (K x N, ldb); each thread owns 4x4
+// output tiles in a strided loop; operands may be in global or shared memory.
+template <typename T>
+__device__ void cta_gemm(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C,
+                         int ldc, bool accumulate) {
+  const int tm = (M + 3) >> 2, tnn = (N + 3) >> 2;
+  for (int t = threadIdx.x; t < tm * tnn; t += blockDim.x) {
+    const int i0 = (t / tnn) * 4, j0 = (t % tnn) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int k = 0; k < K; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = (i0 + a < M) ? A[(size_t)(i0 + a) * lda + k] : (T)0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = (j0 + b < N) ? B[(size_t)k * ldb + j0 + b] : (T)0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (i0 + a >= M) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (j0 + b >= N) continue;
+        T* p = C + (size_t)(i0 + a) * ldc + j0 + b;
+        *p = accumulate ? *p + acc[a][b] : acc[a][b];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Householder QR of A (m x n, lda; typically shared memory, lda = n + 1 to
+// avoid bank conflicts), with Q (m x k, ldq) and R (k x n, ldr) written out,
+// diag(R) >= 0.  Parallel form: per column, the reflector inner products are
+// split over row groups (8 threads per column) and the rank-1 update runs over
+// all elements.  tau/wv: shared scratch of >= n doubles / T.
+template <typename T>
+__device__ void householder_qr_par(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
+                                   double* tau, T* wv, double* red) {
+  // all arithmetic in T: on GB300 FP64 runs at ~1/64 of the FP32 rate
+  const int kk = imin(m, n);
+  const int G = 8;                                 // threads per column in the dot phase
+  __shared__ T s_scale;
+  T* redT = (T*)red;
+  for (int j = 0; j < kk; ++j) {
+    T part = (T)0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+      const T v = A[(size_t)i * lda + j];
+      part += v * v;
+    }
+    const T sig2 = block_sum_t<T>(part, redT);
+    if (threadIdx.x == 0) {
+      const T alpha = A[(size_t)j * lda + j];
+      if (sig2 == (T)0) {
+        tau[j] = 0.0;
+        s_scale = (T)0;
+      } else {
+        const T beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
+        tau[j] = (double)((beta - alpha) / beta);
+        s_scale = (T)1 / (alpha - beta);
+        A[(size_t)j * lda + j] = beta;
+      }
+    }
+    __syncthreads();
+    const T tj = (T)tau[j];
+    if (tj == (T)0) continue;                       // uniform across the block
+    const T sc = s_scale;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
+    __syncthreads();
+    // w_c = A[j][c] + sum_{i>j} v_i A[i][c], c > j
+    const int nc = n - j - 1;
+    // loop bounds uniform over the block so every warp shuffles with all lanes
+    for (int base = 0; base < nc * G; base += blockDim.x) {
+      const int t = base + threadIdx.x;
+      const bool act = t < nc * G;
+      const int c = j + 1 + t / G, p = t % G;
+      T acc = (T)0;
+      if (act) {
+        if (p == 0) acc = A[(size_t)j * lda + c];
+        for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+      if (act && p == 0) wv[c] = acc * tj;
+    }
+    __syncthreads();
+    // A[i][c] -= w_c v_i (v_j = 1)
+    const int rows = m - j;
+    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+      const int ii = j + t / nc, c = j + 1 + t % nc;
+      const T vi = (ii == j) ? (T)1 : A[(size_t)ii * lda + j];
+      A[(size_t)ii * lda + c] -= wv[c] * vi;
+    }
+    __syncthreads();
+  }
+  // R with non-negative diagonal
+  for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
+    const int i = idx / n, c = idx % n;
+    const T d = A[(size_t)i * lda + i] < (T)0 ? (T)-1 : (T)1;
+    R[(size_t)i * ldr + c] = c >= i ? d * A[(size_t)i * lda + c] : (T)0;
+  }
+  // Q = H_0 ... H_{kk-1} [I; 0], backwards
+  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+    const int i = idx / kk, c = idx % kk;
+    Q[(size_t)i * ldq + c] = (i == c) ? (T)1 : (T)0;
+  }
+  __syncthreads();
+  for (int j = kk - 1; j >= 0; --j) {
+    const double tj = tau[j];
+    if (tj == 0.0) continue;
+    const int nc = kk - j;                          // columns j..kk-1
+    for (int base = 0; base < nc * G; base += blockDim.x) {
+      const int t = base + threadIdx.x;
+      const bool act = t < nc * G;
+      const int c = j + t / G, p = t % G;
+      T acc = (T)0;
+      if (act) {
+        if (p == 0) acc = Q[(size_t)j * ldq + c];
+        for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * Q[(size_t)i * ldq + c];
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+      if (act && p == 0) wv[c] = acc * (T)tj;
+    }
+    __syncthreads();
+    const int rows = m - j;
+    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+      const int ii = j + t / nc, c = j + t % nc;
+      const T vi = (ii == j) ? (T)1 : A[(size_t)ii * lda + j];
+      Q[(size_t)ii * ldq + c] -= wv[c] * vi;
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+    const int i = idx / kk, c = idx % kk;
+    if (A[(size_t)c * lda + c] < (T)0) Q[(size_t)i * ldq + c] = -Q[(size_t)i * ldq + c];
+  }
+  __syncthreads();
+}
+
+// One-sided Jacobi as jacobi_cols, with a half-warp per column pair so that a
+// 1024-thread CTA keeps 64 pairs in flight.  Columns have stride ldw >= len.
+template <typename T>
+__device__ int jacobi_cols_hw(T* Wm, int ldw, T* V, int ldv, int ncol, int len, int maxsw) {
+  for (int idx = threadIdx.x; idx < ncol * ncol; idx += blockDim.x)
+    V[(size_t)(idx / ncol) * ldv + idx % ncol] = (idx / ncol == idx % ncol) ? (T)1 : (T)0;
+  __shared__ int s_rot;
+  __syncthreads();
+  if (ncol < 2) return 0;
+  const int np = (ncol + 1) & ~1;
+  const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nhw = blockDim.x >> 4;
+  const unsigned mask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+  const T tolT = (T)(16.0 * Eps<T>::v * sqrt((double)len));
+  int sweep = 0;
+  for (; sweep < maxsw; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int p = hw; p < np / 2; p += nhw) {
+        int a, b;
+        if (p == 0) { a = rnd; b = np - 1; }
+        else { a = (rnd + p) % (np - 1); b = (rnd - p + (np - 1)) % (np - 1); }
+        const bool live = a < ncol && b < ncol;
+        if (a > b) { int t = a; a = b; b = t; }
+        T al = (T)0, be = (T)0, ga = (T)0;
+        T* wa = Wm + (size_t)a * ldw;
+        T* wb = Wm + (size_t)b * ldw;
+        if (live)
+          for (int i = hl; i < len; i += 16) {
+            const T x = wa[i], y = wb[i];
+            al += x * x; be += y * y; ga += x * y;
+          }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(mask, al, o, 16);
+          be += __shfl_xor_sync(mask, be, o, 16);
+          ga += __shfl_xor_sync(mask, ga, o, 16);
+        }
+        // columns below the type's representable range (after the caller's
+        // power-of-two scaling to max |entry| ~ 1) carry nothing
+        // (FP32: below 1e-24 the rotation parameter zeta could overflow)
+        const T floor2 = sizeof(T) == 8 ? (T)1e-250 : (T)1e-24;
+        if (!live || ga == (T)0 || al < floor2 || be < floor2 || fabs(ga) <= tolT * sqrt(al) * sqrt(be))
+          continue;
+        // Rutishauser's rotation zeroing the (a, b) inner product
+        const T zeta = (be - al) / ((T)2 * ga);
+        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + hypot((T)1, zeta));
+        const T cc = (T)1 / sqrt((T)1 + t * t), ss = cc * t;
+        for (int i = hl; i < len; i += 16) {
+          const T x = wa[i], y = wb[i];
+          wa[i] = cc * x - ss * y;
+          wb[i] = ss * x + cc * y;
+        }
+        T* va = V + (size_t)a * ldv;
+        T* vb = V + (size_t)b * ldv;
+        for (int i = hl; i < ncol; i += 16) {
+          const T x = va[i], y = vb[i];
+          va[i] = cc * x - ss * y;
+          vb[i] = ss * x + cc * y;
+        }
+        if (hl == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+}  // namespace tn

@@ -1,0 +1,409 @@
+// Smaller kernels of the MPS-LBM step and of the library's input/output:
+//  - <X, 1>: transfer-vector sweep (Sec. 3.2, mean density rho_0)
+//  - rho_0 and the scalar coefficients of the Taylor 1/rho (Sec. 3.2)
+//  - contraction of an MPS to a dense [x][y][z] field (Eq. MPS), for outputs
+//  - moments and velocity of the contracted populations (Eq. macro, App. A)
+//  - TT-SVD of a dense field (Eq. svd-comp), used to compress geometry masks
+#include <cmath>
+#include <vector>
+
+#include "fit.cuh"
+#include "linalg.cuh"
+
+namespace tn {
+
+// ---------------------------------------------------------------- <X, 1>
+template <typename T>
+__device__ double inner_ones_dev(const MpsRef& X, int L, double* v, double* w) {
+  if (threadIdx.x == 0) v[0] = 1.0;
+  __syncthreads();
+  for (int k = 0; k < L; ++k) {
+    const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
+    const T* A = (const T*)X.base + core_offset(L, X.cap, k);
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) {
+      double acc = 0.0;
+      for (int i = 0; i < r0; ++i)
+        acc += v[i] * ((double)A[((size_t)i * 2) * r1 + j] + (double)A[((size_t)i * 2 + 1) * r1 + j]);
+      w[j] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) v[j] = w[j];
+    __syncthreads();
+  }
+  double r = v[0];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void inner_ones_kernel(const MpsRef* refs, int L, double* out) {
+  __shared__ double v[1024], w[1024];
+  double r = inner_ones_dev<T>(refs[blockIdx.x], L, v, w);
+  if (threadIdx.x == 0) out[blockIdx.x] = r;
+}
+
+template <typename T>
+void launch_inner_ones(const MpsRef* d_refs, int n, int L, double* d_out, cudaStream_t st) {
+  inner_ones_kernel<T><<<n, 256, 0, st>>>(d_refs, L, d_out);
+}
+
+template <typename T>
+__global__ void rho0_kernel(const MpsRef* rho, int L, double n_fluid, double* scal) {
+  __shared__ double v[1024], w[1024];
+  double s = inner_ones_dev<T>(rho[0], L, v, w);
+  if (threadIdx.x == 0) {
+    const double r0 = s / n_fluid;
+    scal[SC_NEG_RHO0] = -r0;
+    scal[SC_INV1] = 1.0 / r0;
+    scal[SC_INV2] = -1.0 / (r0 * r0);
+    scal[SC_INV3] = 1.0 / (r0 * r0 * r0);
+    scal[SC_RHO0] = r0;
+  }
+}
+
+template <typename T>
+void launch_rho0(const MpsRef* d_rho, int L, double n_fluid, double* d_scal, cudaStream_t st) {
+  rho0_kernel<T><<<1, 256, 0, st>>>(d_rho, L, n_fluid, d_scal);
+}
+
+// ---------------------------------------------------------------- copies
+template <typename T>
+__global__ void copy_kernel(const MpsRef* src, const MpsRef* dst, int L) {
+  const MpsRef& S = src[blockIdx.x];
+  const MpsRef& D = dst[blockIdx.x];
+  for (int k = 0; k < L; ++k) {
+    const int r0 = S.ranks[k], r1 = S.ranks[k + 1];
+    const T* a = (const T*)S.base + core_offset(L, S.cap, k);
+    T* b = (T*)D.base + core_offset(L, D.cap, k);
+    for (int i = threadIdx.x; i < r0 * 2 * r1; i += blockDim.x) b[i] = a[i];
+  }
+  for (int k = threadIdx.x; k <= L; k += blockDim.x) D.ranks[k] = S.ranks[k];
+}
+
+template <typename T>
+void launch_copy(const MpsRef* d_src, const MpsRef* d_dst, int n, int L, cudaStream_t st) {
+  if (n > 0) copy_kernel<T><<<n, 256, 0, st>>>(d_src, d_dst, L);
+}
+
+// ---------------------------------------------------------------- dense contraction
+// site-ordered linear index of cell (x, y, z): site k (MSB first) holds bit
+// (n-1-k/3) of coordinate k%3
+__host__ __device__ inline size_t site_index(int x, int y, int z, int n) {
+  size_t idx = 0;
+  const int c[3] = {x, y, z};
+  for (int k = 0; k < 3 * n; ++k) idx = (idx << 1) | (size_t)((c[k % 3] >> (n - 1 - k / 3)) & 1);
+  return idx;
+}
+
+template <typename T>
+__global__ void left_rows_kernel(MpsRef X, int L, int h, T* Lm, int ldl) {
+  __shared__ T v[1024], w[1024];
+  const size_t l = blockIdx.x;
+  for (int k = 0; k < h; ++k) {
+    const int s = (int)((l >> (h - 1 - k)) & 1);
+    const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
+    const T* A = (const T*)X.base + core_offset(L, X.cap, k);
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) {
+      T acc = (T)0;
+      if (k == 0) acc = A[(size_t)s * r1 + j];
+      else for (int i = 0; i < r0; ++i) acc += v[i] * A[((size_t)i * 2 + s) * r1 + j];
+      w[j] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) v[j] = w[j];
+    __syncthreads();
+  }
+  const int rh = X.ranks[h];
+  for (int j = threadIdx.x; j < rh; j += blockDim.x) Lm[l * ldl + j] = v[j];
+}
+
+template <typename T>
+__global__ void right_cols_kernel(MpsRef X, int L, int h, T* Rt, int ldr) {
+  __shared__ T v[1024], w[1024];
+  const size_t q = blockIdx.x;
+  for (int k = L - 1; k >= h; --k) {
+    const int s = (int)((q >> (L - 1 - k)) & 1);
+    const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
+    const T* A = (const T*)X.base + core_offset(L, X.cap, k);
+    for (int i = threadIdx.x; i < r0; i += blockDim.x) {
+      T acc = (T)0;
+      if (k == L - 1) acc = A[(size_t)i * 2 + s];
+      else for (int j = 0; j < r1; ++j) acc += A[((size_t)i * 2 + s) * r1 + j] * v[j];
+      w[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r0; i += blockDim.x) v[i] = w[i];
+    __syncthreads();
+  }
+  const int rh = X.ranks[h];
+  for (int j = threadIdx.x; j < rh; j += blockDim.x) Rt[q * ldr + j] = v[j];
+}
+
+template <typename T>
+__global__ void join_kernel(MpsRef X, int n, int h, const T* Lm, const T* Rt, int ld, T* out) {
+  const int L = 3 * n;
+  const size_t N = (size_t)1 << n;
+  const size_t total = N * N * N;
+  const int rh = X.ranks[h];
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(idx % N), y = (int)((idx / N) % N), x = (int)(idx / (N * N));
+    const size_t si = site_index(x, y, z, n);
+    const size_t l = si >> (L - h), q = si & (((size_t)1 << (L - h)) - 1);
+    const T* a = Lm + l * ld;
+    const T* b = Rt + q * ld;
+    T acc = (T)0;
+    for (int j = 0; j < rh; ++j) acc += a[j] * b[j];
+    out[idx] = acc;
+  }
+}
+
+size_t contract_scratch_bytes(int n_bits, int cap, size_t elem) {
+  const int L = 3 * n_bits, h = L / 2;
+  const size_t ld = bond_cap(L, cap, h);
+  return (((size_t)1 << h) + ((size_t)1 << (L - h))) * ld * elem;
+}
+
+template <typename T>
+int contract_dense(const MpsRef& X, int n_bits, T* d_dense, void* d_scratch, size_t scratch_bytes,
+                   cudaStream_t st) {
+  const int L = 3 * n_bits, h = L / 2;
+  const int ld = bond_cap(L, X.cap, h);
+  if (contract_scratch_bytes(n_bits, X.cap, sizeof(T)) > scratch_bytes) return TNLBM_E_ARG;
+  T* Lm = (T*)d_scratch;
+  T* Rt = Lm + ((size_t)1 << h) * ld;
+  left_rows_kernel<T><<<(unsigned)(1u << h), 256, 0, st>>>(X, L, h, Lm, ld);
+  right_cols_kernel<T><<<(unsigned)(1u << (L - h)), 256, 0, st>>>(X, L, h, Rt, ld);
+  join_kernel<T><<<152 * 16, 256, 0, st>>>(X, n_bits, h, Lm, Rt, ld, d_dense);
+  return 0;
+}
+
+template <typename T>
+__global__ void accum_kernel(const T* f, size_t n, double* rho, double* jx, double* jy, double* jz,
+                             int cx, int cy, int cz, int first) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = (double)f[i];
+    if (first) { rho[i] = v; jx[i] = cx * v; jy[i] = cy * v; jz[i] = cz * v; }
+    else { rho[i] += v; jx[i] += cx * v; jy[i] += cy * v; jz[i] += cz * v; }
+  }
+}
+
+template <typename T>
+void launch_accum_moments(const T* d_f, size_t ncell, double* rho, double* jx, double* jy, double* jz,
+                          int cx, int cy, int cz, int first, cudaStream_t st) {
+  accum_kernel<T><<<152 * 8, 256, 0, st>>>(d_f, ncell, rho, jx, jy, jz, cx, cy, cz, first);
+}
+
+__global__ void velocity_kernel(size_t n, const double* rho, double* jx, double* jy, double* jz,
+                                const double* mask, double fx, double fy, double fz) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double m = mask ? mask[i] : 0.0;
+    const double r = rho[i];
+    if (r > 0.5) {
+      jx[i] = (jx[i] + 0.5 * fx * (1.0 - m)) / r;
+      jy[i] = (jy[i] + 0.5 * fy * (1.0 - m)) / r;
+      jz[i] = (jz[i] + 0.5 * fz * (1.0 - m)) / r;
+    } else {
+      jx[i] = 0.0; jy[i] = 0.0; jz[i] = 0.0;
+    }
+  }
+}
+
+void launch_velocity(size_t ncell, const double* rho, double* jx, double* jy, double* jz,
+                     const double* mask, double fx, double fy, double fz, cudaStream_t st) {
+  velocity_kernel<<<152 * 8, 256, 0, st>>>(ncell, rho, jx, jy, jz, mask, fx, fy, fz);
+}
+
+// ---------------------------------------------------------------- TT-SVD
+template <typename T>
+__global__ void to_site_order_kernel(const T* dense, int n, double* out) {
+  const size_t N = (size_t)1 << n, total = N * N * N;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(idx % N), y = (int)((idx / N) % N), x = (int)(idx / (N * N));
+    out[site_index(x, y, z, n)] = (double)dense[idx];
+  }
+}
+
+// G += M[:, chunk] M[:, chunk]^T over one column chunk per block (upper triangle)
+__global__ void gram_kernel(const double* M, int m, size_t ncols, int kc, double* G) {
+  extern __shared__ double tile[];           // m x kc
+  const size_t c0 = (size_t)blockIdx.x * kc;
+  const int w = (int)((ncols - c0) < (size_t)kc ? (ncols - c0) : (size_t)kc);
+  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) {
+    const int i = e / kc, c = e % kc;
+    tile[e] = c < w ? M[(size_t)i * ncols + c0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    if (j < i) continue;
+    double acc = 0.0;
+    for (int c = 0; c < w; ++c) acc += tile[i * kc + c] * tile[j * kc + c];
+    atomicAdd(&G[(size_t)i * m + j], acc);
+  }
+}
+
+// eigen-decomposition of the symmetric PSD Gram G (m x m) by one-sided Jacobi;
+// truncation; writes U (m x r, FP64) and the rank.
+__global__ void __launch_bounds__(1024) gram_eig_kernel(double* G, int m, double* Wm, double* Vm,
+                                                        double* U, int chi, double delta2,
+                                                        int ncols_cap, int* r_out, int* status) {
+  __shared__ double lam[1024];
+  __shared__ int perm[1024];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e / m, j = e % m;
+    const double v = (j >= i) ? G[(size_t)i * m + j] : G[(size_t)j * m + i];
+    Wm[(size_t)j * m + i] = v;   // column j
+  }
+  __syncthreads();
+  int sw = jacobi_cols<double>(Wm, Vm, m, m, 80);
+  if (sw >= 80 && threadIdx.x == 0) atomicOr(status, ST_NOCONV);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < m; ++i) a += Wm[(size_t)j * m + i] * Wm[(size_t)j * m + i];
+    lam[j] = sqrt(a);                         // eigenvalue of G = sigma^2 of M
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    int rank = 0;
+    for (int o = 0; o < m; ++o) rank += (lam[o] > lam[j]) || (lam[o] == lam[j] && o < j);
+    perm[rank] = j;
+  }
+  __syncthreads();
+  __shared__ int s_r;
+  if (threadIdx.x == 0) {
+    const int rmax = imin(chi, imin(m, ncols_cap));
+    int r = rmax;
+    // eigenvalues of the Gram matrix below its round-off level carry no
+    // information: treat that level as the smallest resolvable tail
+    const double floor2 = 64.0 * 2.220446049250313e-16 * (double)m * lam[perm[0]];
+    const double thr = delta2 > floor2 ? delta2 : floor2;
+    for (int rr = 1; rr <= rmax; ++rr) {
+      double tail = 0.0;
+      for (int p = rr; p < m; ++p) tail += lam[perm[p]];
+      if (tail <= thr) { r = rr; break; }
+    }
+    s_r = r;
+    *r_out = r;
+  }
+  __syncthreads();
+  const int r = s_r;
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int i = e / r, j = e % r;
+    U[e] = Vm[(size_t)perm[j] * m + i];
+  }
+}
+
+// Mn (r x ncols) = U^T (r x m) M (m x ncols)
+__global__ void project_kernel(const double* U, int m, int r, const double* M, size_t ncols, double* Mn) {
+  const size_t total = (size_t)r * ncols;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / ncols);
+    const size_t c = e % ncols;
+    double acc = 0.0;
+    for (int i = 0; i < m; ++i) acc += U[(size_t)i * r + p] * M[(size_t)i * ncols + c];
+    Mn[e] = acc;
+  }
+}
+
+template <typename T>
+__global__ void cast_double_kernel(const T* src, size_t n, double* dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (double)src[i];
+}
+
+template <typename T>
+void launch_cast_double(const T* src, size_t n, double* dst, cudaStream_t st) {
+  cast_double_kernel<T><<<152 * 8, 256, 0, st>>>(src, n, dst);
+}
+
+template <typename T>
+__global__ void cast_store_kernel(const double* src, size_t n, T* dst) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = (T)src[i];
+}
+
+__global__ void norm2_kernel(const double* x, size_t n, double* out) {
+  double a = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a += x[i] * x[i];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+}
+
+template <typename T>
+int tt_svd_dense(const T* d_dense, int n, T* d_dst, int* d_dst_ranks, int dst_cap, int chi_max,
+                 double eps, int* d_status, cudaStream_t st) {
+  const int L = 3 * n;
+  const size_t total = (size_t)1 << L;
+  const int mmax = 2 * imin(chi_max, dst_cap);
+  if (mmax > 1024) return TNLBM_E_ARG;
+  double *M = nullptr, *M2 = nullptr, *G = nullptr, *Wm = nullptr, *Vm = nullptr, *U = nullptr, *nrm = nullptr;
+  int* d_r = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(M); cudaFree(M2); cudaFree(G); cudaFree(Wm); cudaFree(Vm); cudaFree(U); cudaFree(nrm); cudaFree(d_r);
+  };
+  if (cudaMalloc(&M, total * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&M2, total * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&G, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Wm, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&Vm, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&U, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&nrm, sizeof(double)) != cudaSuccess || cudaMalloc(&d_r, sizeof(int)) != cudaSuccess) {
+    cleanup();
+    return TNLBM_E_OOM;
+  }
+  to_site_order_kernel<T><<<152 * 8, 256, 0, st>>>(d_dense, n, M);
+  cudaMemsetAsync(nrm, 0, sizeof(double), st);
+  norm2_kernel<<<152 * 4, 256, 0, st>>>(M, total, nrm);
+  double h_n2 = 0.0;
+  cudaMemcpyAsync(&h_n2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  const double delta = eps * sqrt(h_n2) / sqrt((double)(L - 1));
+  std::vector<int> ranks(L + 1, 1);
+  int r = 1;
+  for (int k = 0; k < L - 1; ++k) {
+    const int m = 2 * r;
+    const size_t ncols = total >> (k + 1);
+    cudaMemsetAsync(G, 0, (size_t)m * m * sizeof(double), st);
+    int kc = 6144 / m;
+    if (kc < 1) kc = 1;
+    const size_t nblk = (ncols + kc - 1) / kc;
+    gram_kernel<<<(unsigned)nblk, 256, (size_t)m * kc * sizeof(double), st>>>(M, m, ncols, kc, G);
+    gram_eig_kernel<<<1, 1024, 0, st>>>(G, m, Wm, Vm, U, imin(chi_max, dst_cap), delta * delta,
+                                        (int)(ncols < (size_t)1024 ? ncols : (size_t)1024), d_r, d_status);
+    int h_r = 0;
+    cudaMemcpyAsync(&h_r, d_r, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { cleanup(); return cuda_fail(e, "tt_svd_dense"); }
+    const int rn = h_r;
+    if (rn > bond_cap(L, dst_cap, k + 1)) { cleanup(); return TNLBM_E_CAPACITY; }
+    // core k = U (r x 2 x rn)
+    cast_store_kernel<T><<<64, 256, 0, st>>>(U, (size_t)m * rn, d_dst + core_offset(L, dst_cap, k));
+    project_kernel<<<152 * 8, 256, 0, st>>>(U, m, rn, M, ncols, M2);
+    double* t = M; M = M2; M2 = t;
+    r = rn;
+    ranks[k + 1] = rn;
+  }
+  cast_store_kernel<T><<<64, 256, 0, st>>>(M, (size_t)2 * r, d_dst + core_offset(L, dst_cap, L - 1));
+  cudaMemcpyAsync(d_dst_ranks, ranks.data(), (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "tt_svd_dense");
+  return 0;
+}
+
+#define INST(T)                                                                                   \
+  template void launch_inner_ones<T>(const MpsRef*, int, int, double*, cudaStream_t);           \
+  template void launch_rho0<T>(const MpsRef*, int, double, double*, cudaStream_t);              \
+  template void launch_copy<T>(const MpsRef*, const MpsRef*, int, int, cudaStream_t);           \
+  template int contract_dense<T>(const MpsRef&, int, T*, void*, size_t, cudaStream_t);          \
+  template void launch_accum_moments<T>(const T*, size_t, double*, double*, double*, double*,   \
+                                        int, int, int, int, cudaStream_t);                       \
+  template int tt_svd_dense<T>(const T*, int, T*, int*, int, int, double, int*, cudaStream_t); \
+  template void launch_cast_double<T>(const T*, size_t, double*, cudaStream_t);
+INST(float)
+INST(double)
+
+}  // namespace tn

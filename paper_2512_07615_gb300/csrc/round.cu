@@ -1,0 +1,472 @@
+// TT-rounding of linear combinations of exactly formed terms (one CTA per job).
+//
+// For a job sum_t coef_t X_t the wide MPS is the block-diagonal sum of Eq. (add);
+// its cores are never stored as a whole: at site k the term blocks are formed
+// (plain copy, rank-1 mask product, Kronecker product of Eq. (mul), or the shift
+// MPO x MPS contraction of Eq. (applympo) with the cores of Sec. 2.5), multiplied
+// from the left by the R factor carried from site k-1, and QR-factorised
+// (left-orthogonalising sweep, Eq. lorg).  The right-to-left sweep then moves the
+// canonical centre back to site 0 with SVDs (Eq. svd-move) and truncates at the
+// centre to chi / eps.
+#include "linalg.cuh"
+
+namespace tn {
+
+static constexpr int RT = 1024;                     // threads per rounding CTA
+static constexpr int SM_SMALL = 44 * 1024;          // bookkeeping part of smem
+static constexpr int SM_WORK = 176 * 1024;          // work area in smem
+static constexpr int MAXK = 1024;                   // max columns of a QR / SVD
+
+size_t round_smem_bytes() { return SM_SMALL + SM_WORK; }
+
+// ---------------------------------------------------------------- layout (host)
+void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
+  for (int k = 0; k <= L; ++k) {
+    int s = 0;
+    for (int t = 0; t < j.nterms; ++t) s += term_bond_bound(j.t[t], L, n_bits, k);
+    j.rw[k] = (k == 0 || k == L) ? 1 : s;
+  }
+  // QR-sweep bonds: q_0 = 1, q_{k+1} <= min(2 q_k, rw_{k+1})
+  j.qb[0] = 1;
+  for (int k = 0; k < L; ++k) j.qb[k + 1] = imin(2 * j.qb[k], j.rw[k + 1]);
+  j.qb[L] = 1;
+  size_t off = 0;
+  auto al = [&](size_t n) { size_t o = off; off += (n + 31) & ~(size_t)31; return o; };
+  for (int k = 0; k < L; ++k) j.lay.q_off[k] = al((size_t)2 * j.qb[k] * (k == L - 1 ? 1 : j.qb[k + 1]));
+  size_t wmax = 0, mmax = 0, rmax = 0, cmax = 0, jw = 0, jv = 0, us = 0;
+  for (int k = 0; k < L; ++k) {
+    size_t w = 0;
+    for (int t = 0; t < j.nterms; ++t)
+      w += (size_t)term_bond_bound(j.t[t], L, n_bits, k) * 2 * term_bond_bound(j.t[t], L, n_bits, k + 1);
+    wmax = w > wmax ? w : wmax;
+    size_t m = (size_t)j.qb[k] * 2 * j.rw[k + 1];
+    mmax = m > mmax ? m : mmax;
+    size_t r = (size_t)j.qb[k + 1] * j.rw[k + 1];
+    rmax = r > rmax ? r : rmax;
+    // right sweep at site k: C is q_k x 2 r_{k+1}, r_{k+1} <= min(chi, q_{k+1})
+    size_t rn = (size_t)imin(j.chi, j.qb[k + 1]);
+    size_t cm = (size_t)j.qb[k] * 2 * rn;
+    cmax = cm > cmax ? cm : cmax;
+    size_t ncol = imin(j.qb[k], (int)(2 * rn));
+    size_t len = j.qb[k] > (int)(2 * rn) ? j.qb[k] : 2 * rn;
+    jw = ncol * len > jw ? ncol * len : jw;
+    jv = ncol * ncol > jv ? ncol * ncol : jv;
+    size_t u = (size_t)j.qb[k] * imin(j.chi, (int)ncol);
+    us = u > us ? u : us;
+    // C' = Q_{k-1} (2 q_{k-1} x q_k) * US: 2 q_{k-1} x r
+    size_t c2 = (size_t)(k > 0 ? j.qb[k - 1] : 1) * 2 * imin(j.chi, (int)ncol);
+    cmax = c2 > cmax ? c2 : cmax;
+  }
+  j.lay.w_off = al(wmax);
+  j.lay.m_off = al(mmax);
+  j.lay.r_off = al(rmax > 1 ? rmax : 1);
+  j.lay.c_off = al(cmax);
+  j.lay.jw_off = al(jw);
+  j.lay.jv_off = al(jv);
+  j.lay.us_off = al(us);
+  j.lay.total = off;
+  (void)eb;
+}
+
+// ---------------------------------------------------------------- device helpers
+__device__ inline void flag(int* st, int code) { atomicOr(st, code); }
+
+template <typename T>
+__device__ inline const T* core_ptr(const MpsRef& m, int L, int k) {
+  return (const T*)m.base + core_offset(L, m.cap, k);
+}
+
+// Input index s of the shift MPO block (w, s_out, w') at site k, or -1 (zero).
+// 1-D cores (Sec. 2.5): first [I X], middle [[I j],[0 j']], last [j; j'],
+// X = P (cyclic) or j (non-cyclic); (j, j') = (J, J') for offset +1, swapped for -1.
+// Non-axis sites carry the identity and pass the bond through.
+__device__ inline int shift_src(const Term& t, int n_bits, int k, int w, int so, int w2) {
+  if (k % 3 != t.axis) return (w == w2) ? so : -1;             // identity padding
+  const int lev = k / 3;
+  // 2x2 blocks as functions out -> in: I: s; J: out0<-in1; J': out1<-in0; P: 1-s
+  const int jJ = (t.offset == 1) ? 0 : 1;   // 0: j = J, 1: j = J'
+  auto blockJ = [&](int which) -> int {     // which 0 = j, 1 = j'
+    int isJ = (which == 0) ? (jJ == 0) : (jJ == 1);
+    if (isJ) return so == 0 ? 1 : -1;      // J: (0,1)
+    return so == 1 ? 0 : -1;               // J': (1,0)
+  };
+  if (n_bits == 1) {                        // single 2x2 operator
+    if (t.cyclic) return 1 - so;
+    return blockJ(0);
+  }
+  if (lev == 0) {                           // [I  X], 1 x 2
+    if (w2 == 0) return so;
+    if (t.cyclic) return 1 - so;
+    return blockJ(0);
+  }
+  if (lev == n_bits - 1) {                  // [j; j'], 2 x 1
+    return blockJ(w == 0 ? 0 : 1);
+  }
+  if (w == 0 && w2 == 0) return so;         // [[I j],[0 j']]
+  if (w == 0 && w2 == 1) return blockJ(0);
+  if (w == 1 && w2 == 1) return blockJ(1);
+  return -1;
+}
+
+__device__ inline int shift_w(const Term& t, int n_bits, int k) {   // MPO bond at bond k
+  int first = t.axis, last = t.axis + 3 * (n_bits - 1);
+  return (k > first && k <= last) ? 2 : 1;
+}
+
+__device__ inline int term_bond(const Term& t, int n_bits, int k) {
+  switch (t.kind) {
+    case T_ONES: return 1;
+    case T_PLAIN:
+    case T_MASK1: return t.x.ranks[k];
+    case T_KRON: return t.x.ranks[k] * t.y.ranks[k];
+    case T_SHIFT: return shift_w(t, n_bits, k) * t.x.ranks[k];
+  }
+  return 0;
+}
+
+// element (i, s, j) of term t's core k (coefficient not applied)
+template <typename T>
+__device__ inline T term_elem(const Term& t, int L, int n_bits, int k, int i, int s, int j,
+                              const T* masks) {
+  switch (t.kind) {
+    case T_ONES: return (T)1;
+    case T_PLAIN: {
+      const int r1 = t.x.ranks[k + 1];
+      return core_ptr<T>(t.x, L, k)[((size_t)i * 2 + s) * r1 + j];
+    }
+    case T_MASK1: {
+      const int r1 = t.x.ranks[k + 1];
+      return core_ptr<T>(t.x, L, k)[((size_t)i * 2 + s) * r1 + j] *
+             masks[((size_t)t.mask_id * TN_MAXL + k) * 2 + s];
+    }
+    case T_KRON: {
+      const int rb = t.y.ranks[k], rb1 = t.y.ranks[k + 1], ra1 = t.x.ranks[k + 1];
+      const int a = i / rb, b = i % rb, a1 = j / rb1, b1 = j % rb1;
+      return core_ptr<T>(t.x, L, k)[((size_t)a * 2 + s) * ra1 + a1] *
+             core_ptr<T>(t.y, L, k)[((size_t)b * 2 + s) * rb1 + b1];
+    }
+    case T_SHIFT: {
+      const int ra = t.x.ranks[k], ra1 = t.x.ranks[k + 1];
+      const int w = i / ra, a = i % ra, w2 = j / ra1, a1 = j % ra1;
+      const int si = shift_src(t, n_bits, k, w, s, w2);
+      if (si < 0) return (T)0;
+      return core_ptr<T>(t.x, L, k)[((size_t)a * 2 + si) * ra1 + a1];
+    }
+  }
+  return (T)0;
+}
+
+// ---------------------------------------------------------------- the kernel
+// Shared memory map (bytes): [0,16K) bond bookkeeping; then 32 doubles of
+// reduction scratch, tau[MAXK], sig[MAXK] (doubles), wv[MAXK] (T); the rest is
+// the work area holding the QR panel (left sweep) or the Jacobi pair W, V
+// (right sweep) whenever they fit.
+static constexpr int SM_RED = 16 * 1024;
+static constexpr int SM_TAU = SM_RED + 256;
+static constexpr int SM_SIG = SM_TAU + (MAXK + 8) * 8;   // tau also holds tails at [2, MAXK+2)
+static constexpr int SM_WV = SM_SIG + MAXK * 8;
+static_assert(SM_WV + MAXK * 8 <= SM_SMALL, "bookkeeping overlaps the work area");
+static_assert(16 * 1024 >= (2 * TN_MAXT * (TN_MAXL + 1) + TN_MAXT + 2 * (TN_MAXL + 1) + MAXK) * 4, "bond tables");
+
+template <typename T>
+__global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L,
+                                                   int n_bits, const T* __restrict__ masks,
+                                                   const double* __restrict__ scal,
+                                                   int* __restrict__ status,
+                                                   double* __restrict__ ctr) {
+  const RoundJob& J = jobs[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* s_rt = (int*)smem;                            // [TN_MAXT][TN_MAXL+1] term bonds
+  int* s_ro = s_rt + TN_MAXT * (TN_MAXL + 1);        // row offsets at each bond
+  int* s_wo = s_ro + TN_MAXT * (TN_MAXL + 1);        // per-term offsets in W buffer
+  int* s_R = s_wo + TN_MAXT;                         // wide bonds
+  int* s_q = s_R + TN_MAXL + 1;                      // QR sweep bonds
+  int* s_perm = s_q + TN_MAXL + 1;                   // [MAXK]
+  double* s_red = (double*)(smem + SM_RED);
+  double* s_tau = (double*)(smem + SM_TAU);
+  double* s_sig = (double*)(smem + SM_SIG);
+  T* s_wv = (T*)(smem + SM_WV);
+  T* work = (T*)(smem + SM_SMALL);
+  __shared__ double s_coef[TN_MAXT];
+  __shared__ int s_bad, s_rank;
+
+  const int nt = J.nterms;
+  T* scr = (T*)J.scratch;
+  double flops = 0.0;                                  // thread 0 only
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  // ---- bonds of every term and of the wide sum
+  for (int idx = threadIdx.x; idx < nt * (L + 1); idx += blockDim.x) {
+    const int t = idx / (L + 1), k = idx % (L + 1);
+    const Term& tm = J.t[t];
+    int rb = term_bond(tm, n_bits, k);
+    if (tm.kind != T_ONES) {
+      if (tm.x.ranks[k] > bond_cap(L, tm.x.cap, k) || tm.x.ranks[k] < 1) s_bad = 1;
+      if (tm.kind == T_KRON && (tm.y.ranks[k] > bond_cap(L, tm.y.cap, k) || tm.y.ranks[k] < 1)) s_bad = 1;
+    }
+    s_rt[t * (TN_MAXL + 1) + k] = rb;
+  }
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    double c = J.t[t].coef;
+    if (J.t[t].coef_slot >= 0) c *= scal[J.t[t].coef_slot];
+    s_coef[t] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k <= L; ++k) {
+      int acc = 0;
+      for (int t = 0; t < nt; ++t) {
+        s_ro[t * (TN_MAXL + 1) + k] = (k == 0 || k == L) ? 0 : acc;
+        acc += s_rt[t * (TN_MAXL + 1) + k];
+      }
+      s_R[k] = (k == 0 || k == L) ? 1 : acc;
+      if (s_R[k] > J.rw[k]) s_bad = 1;
+    }
+  }
+  __syncthreads();
+  if (s_bad) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+
+  // ---- materialise a single term without rounding
+  if (J.materialize_only) {
+    const Term& tm = J.t[0];
+    for (int k = 0; k < L; ++k) {
+      const int r0 = s_rt[k], r1 = s_rt[k + 1];
+      if (r0 > bond_cap(L, J.dst.cap, k) || r1 > bond_cap(L, J.dst.cap, k + 1)) {
+        if (threadIdx.x == 0) flag(status, ST_CAPACITY);
+        return;
+      }
+      T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
+      const T cf = (T)(k == 0 ? s_coef[0] : 1.0);
+      for (int idx = threadIdx.x; idx < r0 * 2 * r1; idx += blockDim.x) {
+        int i = idx / (2 * r1), s = (idx / r1) % 2, jj = idx % r1;
+        out[idx] = cf * term_elem<T>(tm, L, n_bits, k, i, s, jj, masks);
+      }
+    }
+    for (int k = threadIdx.x; k <= L; k += blockDim.x) J.dst.ranks[k] = s_rt[k];
+    return;
+  }
+
+  // ---- left-orthogonalising sweep over the wide sum
+  T* Rc = scr + J.lay.r_off;                // carried R factor, rc x R_k (ld R_k)
+  if (threadIdx.x == 0) { Rc[0] = (T)1; s_q[0] = 1; }
+  __syncthreads();
+  int rc = 1;
+  for (int k = 0; k < L; ++k) {
+    const int Rk = s_R[k], Rk1 = s_R[k + 1];
+    // (a) term blocks of core k into W (global scratch)
+    T* W = scr + J.lay.w_off;
+    if (threadIdx.x == 0) {
+      int o = 0;
+      for (int t = 0; t < nt; ++t) {
+        s_wo[t] = o;
+        o += s_rt[t * (TN_MAXL + 1) + k] * 2 * s_rt[t * (TN_MAXL + 1) + k + 1];
+      }
+    }
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const int r0 = s_rt[t * (TN_MAXL + 1) + k], r1 = s_rt[t * (TN_MAXL + 1) + k + 1];
+      const T cf = (T)(k == 0 ? s_coef[t] : 1.0);
+      T* Wt = W + s_wo[t];
+      for (int idx = threadIdx.x; idx < r0 * 2 * r1; idx += blockDim.x) {
+        int i = idx / (2 * r1), s = (idx / r1) % 2, jj = idx % r1;
+        Wt[idx] = cf * term_elem<T>(J.t[t], L, n_bits, k, i, s, jj, masks);
+      }
+    }
+    __syncthreads();
+    // (b) M = Rc * blockdiag(W): rows (r, s), row length Rk1, leading dim ld
+    const int mrows = 2 * rc;
+    int ld = Rk1 | 1;
+    bool in_smem = (size_t)mrows * ld * sizeof(T) <= (size_t)SM_WORK;
+    if (!in_smem) ld = Rk1;
+    T* M = in_smem ? work : scr + J.lay.m_off;
+    const bool last = (k == L - 1);
+    if (last)
+      for (int idx = threadIdx.x; idx < mrows * ld; idx += blockDim.x) M[idx] = (T)0;
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+      const int r0 = s_rt[t * (TN_MAXL + 1) + k], r1 = s_rt[t * (TN_MAXL + 1) + k + 1];
+      const int co = s_ro[t * (TN_MAXL + 1) + k + 1], ro = s_ro[t * (TN_MAXL + 1) + k];
+      const T* Wt = W + s_wo[t];
+      for (int s = 0; s < 2; ++s)
+        cta_gemm<T>(rc, r1, r0, Rc + ro, Rk, Wt + s * r1, 2 * r1, M + (size_t)s * ld + co, 2 * ld, last);
+      if (threadIdx.x == 0) flops += 4.0 * rc * r0 * r1;
+    }
+    T* Qk = scr + J.lay.q_off[k];
+    if (last) {
+      for (int idx = threadIdx.x; idx < mrows; idx += blockDim.x) Qk[idx] = M[(size_t)idx * ld];
+      __syncthreads();
+      break;
+    }
+    // (c) QR of M (mrows x Rk1) -> Q_k (ld rq), new carried R (rq x Rk1, ld Rk1)
+    const int rq = imin(mrows, Rk1);
+    if (rq > MAXK || Rk1 > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+    householder_qr_par<T>(M, mrows, Rk1, ld, Qk, rq, Rc, Rk1, s_tau, s_wv, s_red);
+    if (threadIdx.x == 0) flops += qr_flops(mrows, Rk1);
+    rc = rq;
+    if (threadIdx.x == 0) s_q[k + 1] = rq;
+    __syncthreads();
+    (void)Rk;
+  }
+  if (threadIdx.x == 0) s_q[L] = 1;
+  __syncthreads();
+
+  // ---- right-to-left truncated SVD sweep
+  T* C = scr + J.lay.c_off;
+  {
+    const int q = s_q[L - 1];
+    const T* Ql = scr + J.lay.q_off[L - 1];
+    double part = 0.0;
+    for (int idx = threadIdx.x; idx < 2 * q; idx += blockDim.x) {
+      double v = (double)Ql[idx];
+      part += v * v;
+      C[idx] = Ql[idx];
+    }
+    double nrm2 = block_sum(part, s_red);
+    if (!isfinite(nrm2)) { if (threadIdx.x == 0) flag(status, ST_NAN); }
+    if (threadIdx.x == 0) s_tau[0] = J.eps * sqrt(nrm2) / sqrt((double)(L - 1));
+    __syncthreads();
+  }
+  const double delta = s_tau[0];
+  __syncthreads();
+  int rnext = 1;
+  for (int k = L - 1; k >= 1; --k) {
+    const int m = s_q[k], n = 2 * rnext;
+    const int ncol = imin(m, n), len = imax(m, n);
+    if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+    const bool trans = (n <= m);             // Jacobi on the columns of C
+    const int ldw = len | 1, ldv = ncol | 1;
+    const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(T);
+    T* Wm = (need <= (size_t)SM_WORK) ? work : scr + J.lay.jw_off;
+    T* Vm = (need <= (size_t)SM_WORK) ? work + (size_t)ncol * ldw : scr + J.lay.jv_off;
+    const int ldw_e = (need <= (size_t)SM_WORK) ? ldw : len;
+    const int ldv_e = (need <= (size_t)SM_WORK) ? ldv : ncol;
+    // scale by an exact power of two so that max |C| is in [1, 2): keeps the
+    // Jacobi inner products far from under- and overflow; undone exactly below
+    T amax = (T)0;
+    for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) amax = fmax(amax, fabs(C[idx]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)amax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, s_red[w]);
+      int e = 0;
+      if (a > 0.0 && isfinite(a)) frexp(a, &e);
+      s_tau[1] = ldexp(1.0, 1 - e);     // scale
+    }
+    __syncthreads();
+    const double scl = s_tau[1];
+    const T tscl = (T)scl;
+    for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
+      const int jj = idx / len, i = idx % len;
+      Wm[(size_t)jj * ldw_e + i] = tscl * (trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]);
+    }
+    __syncthreads();
+    const int maxsw = 60;
+    int sw = jacobi_cols_hw<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
+    if (sw >= maxsw && threadIdx.x == 0) {
+      flag(status, ST_NOCONV);
+      if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big
+        status[2] = blockIdx.x; status[3] = k; status[4] = ncol; status[5] = len;
+      }
+    }
+    for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+      T a = (T)0;
+      const T* w = Wm + (size_t)jj * ldw_e;
+      for (int i = 0; i < len; ++i) a += w[i] * w[i];
+      s_sig[jj] = (double)sqrt(a) / scl;         // singular value of the unscaled C
+    }
+    __syncthreads();
+    for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+      int rank = 0;
+      const double sj = s_sig[jj];
+      for (int o = 0; o < ncol; ++o) {
+        const double so = s_sig[o];
+        rank += (so > sj) || (so == sj && o < jj);
+      }
+      s_perm[rank] = jj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // smallest r in [1, min(chi, ncol)] with discarded tail <= delta (FP64 tail)
+      const int rmax = imin(J.chi, ncol);
+      double tail2 = 0.0;
+      int r = rmax;
+      for (int p = ncol - 1; p >= 1; --p) {
+        const double sv = s_sig[s_perm[p]];
+        tail2 += sv * sv;
+        s_tau[2 + p] = tail2;                  // tail starting at position p
+      }
+      for (int rr = 1; rr <= rmax; ++rr) {
+        const double t2 = (rr < ncol) ? s_tau[2 + rr] : 0.0;
+        if (sqrt(t2) <= delta) { r = rr; break; }
+      }
+      if (r > bond_cap(L, J.dst.cap, k)) { s_bad = 1; r = bond_cap(L, J.dst.cap, k); }
+      s_rank = r;
+      flops += svd_flops(m, n);
+    }
+    __syncthreads();
+    if (s_bad) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+    const int r = s_rank;
+    // outputs: core k = V^T[:r] (r x n) into dst; US (m x r) into scratch
+    T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
+    T* US = scr + J.lay.us_off;
+    for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) {
+      const int jr = idx / n, c = idx % n;
+      const int pj = s_perm[jr];
+      T v;
+      if (trans) {
+        v = Vm[(size_t)pj * ldv_e + c];
+      } else {
+        const T sg = (T)(s_sig[pj] * scl);       // norm of the scaled column
+        v = sg > (T)0 ? Wm[(size_t)pj * ldw_e + c] / sg : (T)(c == jr ? 1 : 0);
+      }
+      out[idx] = v;
+    }
+    for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) {
+      const int i = idx / r, jr = idx % r;
+      const int pj = s_perm[jr];
+      US[idx] = trans ? Wm[(size_t)pj * ldw_e + i] * (T)(1.0 / scl)
+                      : Vm[(size_t)pj * ldv_e + i] * (T)s_sig[pj];
+    }
+    if (threadIdx.x == 0) J.dst.ranks[k] = r;
+    __syncthreads();
+    // C' = Q_{k-1} (2 q_{k-1} x m) * US (m x r)
+    const int rows = 2 * s_q[k - 1];
+    const T* Qp = scr + J.lay.q_off[k - 1];
+    cta_gemm<T>(rows, r, m, Qp, m, US, r, C, r, false);
+    if (threadIdx.x == 0) flops += 2.0 * rows * m * r;
+    rnext = r;
+  }
+  // core 0 = C (1 x 2 x r_1)
+  {
+    T* out = (T*)J.dst.base;
+    for (int idx = threadIdx.x; idx < 2 * rnext; idx += blockDim.x) out[idx] = C[idx];
+    if (threadIdx.x == 0) {
+      J.dst.ranks[0] = 1;
+      J.dst.ranks[L] = 1;
+      if (ctr) atomicAdd(&ctr[C_ROUND], flops);
+    }
+  }
+}
+
+template <typename T>
+void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T* d_masks,
+                  const double* d_scal, int* d_status, cudaStream_t st, double* d_ctr) {
+  if (njobs <= 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)round_smem_bytes());
+    attr_set = true;
+  }
+  round_kernel<T><<<njobs, RT, round_smem_bytes(), st>>>(d_jobs, L, n_bits, d_masks, d_scal,
+                                                         d_status, d_ctr);
+}
+
+template void launch_round<float>(const RoundJob*, int, int, int, const float*, const double*,
+                                  int*, cudaStream_t, double*);
+template void launch_round<double>(const RoundJob*, int, int, int, const double*,
+                                   const double*, int*, cudaStream_t, double*);
+
+}  // namespace tn

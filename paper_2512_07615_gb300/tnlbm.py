@@ -1,0 +1,301 @@
+"""Python-side marshalling for libtnlbm: device MPS buffers (torch tensors in the
+flat layout of include/tnlbm.h), the simulation handle, and the batched
+primitives.  No arithmetic of the method happens here."""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import native as nat
+
+_DT = {nat.FP64: torch.float64, nat.FP32: torch.float32}
+
+
+def mps_size(L, cap):
+    return int(nat.lib().tnlbm_mps_size(L, cap))
+
+
+def mps_offset(L, cap, k):
+    return int(nat.lib().tnlbm_mps_offset(L, cap, k))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptrs(items):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = t.data_ptr()
+    return arr
+
+
+class DeviceMps:
+    """One MPS in device memory: `data` holds the flat layout with capacity
+    `cap`, `ranks` the realised bonds r[0..L] (int32)."""
+
+    def __init__(self, L, cap, precision=nat.FP64, device="cuda"):
+        self.L, self.cap, self.precision = L, cap, precision
+        self.data = torch.zeros(mps_size(L, cap), dtype=_DT[precision], device=device)
+        self.ranks = torch.ones(L + 1, dtype=torch.int32, device=device)
+
+    @classmethod
+    def from_cores(cls, cores, cap=None, precision=nat.FP64, device="cuda"):
+        L = len(cores)
+        r = [1] + [c.shape[2] for c in cores]
+        cap = cap or max(r)
+        m = cls(L, cap, precision, device)
+        flat = np.zeros(mps_size(L, cap))
+        for k, c in enumerate(cores):
+            o = mps_offset(L, cap, k)
+            flat[o:o + c.size] = np.asarray(c, dtype=np.float64).reshape(-1)
+        m.data.copy_(torch.from_numpy(flat).to(_DT[precision]))
+        m.ranks.copy_(torch.tensor(r, dtype=torch.int32))
+        return m
+
+    def cores(self):
+        flat = self.data.double().cpu().numpy()
+        r = self.ranks.cpu().numpy().tolist()
+        out = []
+        for k in range(self.L):
+            o = mps_offset(self.L, self.cap, k)
+            out.append(flat[o:o + r[k] * 2 * r[k + 1]].reshape(r[k], 2, r[k + 1]).copy())
+        return out
+
+    def bonds(self):
+        return self.ranks.cpu().numpy().tolist()
+
+
+def _term(kind, coef=1.0, x=None, y=None, axis=0, offset=1, cyclic=1, mask=None):
+    t = nat.Term()
+    t.kind = kind
+    t.coef = coef
+    if x is not None:
+        t.x, t.x_ranks, t.x_cap = x.data.data_ptr(), x.ranks.data_ptr(), x.cap
+    if y is not None:
+        t.y, t.y_ranks, t.y_cap = y.data.data_ptr(), y.ranks.data_ptr(), y.cap
+    t.axis, t.offset, t.cyclic = axis, offset, cyclic
+    keep = None
+    if mask is not None:
+        keep = np.ascontiguousarray(mask, dtype=np.float64).reshape(-1)
+        t.mask = keep.ctypes.data_as(nat.c_double_p)
+    return t, keep
+
+
+def plain(x, coef=1.0):
+    return dict(kind=nat.TERM_PLAIN, coef=coef, x=x)
+
+
+def ones(coef=1.0):
+    return dict(kind=nat.TERM_ONES, coef=coef)
+
+
+def shift(x, axis, offset, cyclic=True, coef=1.0):
+    return dict(kind=nat.TERM_SHIFT, coef=coef, x=x, axis=axis, offset=offset, cyclic=int(cyclic))
+
+
+def mask1(x, vectors, coef=1.0):
+    return dict(kind=nat.TERM_MASK1, coef=coef, x=x, mask=vectors)
+
+
+def kron(x, y, coef=1.0):
+    return dict(kind=nat.TERM_KRON, coef=coef, x=x, y=y)
+
+
+def _terms_array(batches):
+    nterms = len(batches[0])
+    arr = (nat.Term * (len(batches) * nterms))()
+    keep = []
+    for b, terms in enumerate(batches):
+        assert len(terms) == nterms
+        for t, spec in enumerate(terms):
+            tm, k = _term(**spec)
+            arr[b * nterms + t] = tm
+            keep.append(k)
+    return arr, nterms, keep
+
+
+def lincomb_round(batches, dst, chi_max, eps, stream=None):
+    """dst[b] = round(sum of batches[b]) (tnlbm_lincomb_round)."""
+    arr, nterms, keep = _terms_array(batches)
+    p = dst[0].precision
+    rc = nat.lib().tnlbm_lincomb_round(p, dst[0].L // 3, len(dst), nterms, arr,
+                                       _ptrs([d.data for d in dst]), _ptrs([d.ranks for d in dst]),
+                                       dst[0].cap, chi_max, eps, _stream(stream))
+    nat.check(rc, "tnlbm_lincomb_round")
+
+
+def materialize(terms, dst, stream=None):
+    arr, _, keep = _terms_array([[t] for t in terms])
+    p = dst[0].precision
+    rc = nat.lib().tnlbm_materialize(p, dst[0].L // 3, len(dst), arr, _ptrs([d.data for d in dst]),
+                                     _ptrs([d.ranks for d in dst]), dst[0].cap, _stream(stream))
+    nat.check(rc, "tnlbm_materialize")
+
+
+def hadamard_fit(B, C, A, sweeps=2, stream=None):
+    p = A[0].precision
+    rc = nat.lib().tnlbm_hadamard_fit(p, A[0].L // 3, len(A),
+                                      _ptrs([x.data for x in B]), _ptrs([x.ranks for x in B]), B[0].cap,
+                                      _ptrs([x.data for x in C]), _ptrs([x.ranks for x in C]), C[0].cap,
+                                      _ptrs([x.data for x in A]), _ptrs([x.ranks for x in A]), A[0].cap,
+                                      sweeps, _stream(stream))
+    nat.check(rc, "tnlbm_hadamard_fit")
+
+
+def inner_ones(X, stream=None):
+    out = torch.zeros(len(X), dtype=torch.float64, device=X[0].data.device)
+    rc = nat.lib().tnlbm_inner_ones(X[0].precision, X[0].L // 3, len(X), _ptrs([x.data for x in X]),
+                                    _ptrs([x.ranks for x in X]), X[0].cap, ctypes.c_void_p(out.data_ptr()),
+                                    _stream(stream))
+    nat.check(rc, "tnlbm_inner_ones")
+    return out
+
+
+def to_dense(X, stream=None):
+    n = X.L // 3
+    N = 1 << n
+    out = torch.empty((N, N, N), dtype=X.data.dtype, device=X.data.device)
+    rc = nat.lib().tnlbm_to_dense(X.precision, n, ctypes.c_void_p(X.data.data_ptr()),
+                                  ctypes.c_void_p(X.ranks.data_ptr()), X.cap,
+                                  ctypes.c_void_p(out.data_ptr()), _stream(stream))
+    nat.check(rc, "tnlbm_to_dense")
+    return out
+
+
+def from_dense(dense, cap, chi_max, eps, stream=None):
+    n = int(dense.shape[0]).bit_length() - 1
+    p = nat.FP64 if dense.dtype == torch.float64 else nat.FP32
+    X = DeviceMps(3 * n, cap, p, dense.device)
+    d = dense.contiguous()
+    rc = nat.lib().tnlbm_from_dense(p, n, ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(X.data.data_ptr()),
+                                    ctypes.c_void_p(X.ranks.data_ptr()), cap, chi_max, eps, _stream(stream))
+    nat.check(rc, "tnlbm_from_dense")
+    return X
+
+
+class Sim:
+    """Handle of a tnlbm_sim (tnlbm_create ... tnlbm_destroy)."""
+
+    def __init__(self, n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
+                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
+                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None):
+        c = nat.Config()
+        c.n_per_axis = n_per_axis
+        c.lattice = lattice
+        c.tau = tau
+        for d in range(3):
+            c.periodic[d] = int(periodic[d])
+            c.force[d] = float(force[d])
+        self._keep = []
+        if solid is not None:
+            s = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+            self._keep.append(s)
+            c.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        c.chi_mask = chi_mask
+        c.eps_mask = eps_mask
+        if mask_cores is not None:
+            L = len(mask_cores)
+            r = [1] + [x.shape[2] for x in mask_cores]
+            cap = max(r)
+            flat = np.zeros(mps_size(L, cap))
+            for k, x in enumerate(mask_cores):
+                o = mps_offset(L, cap, k)
+                flat[o:o + x.size] = x.reshape(-1)
+            rr = np.array(r, dtype=np.int32)
+            self._keep += [flat, rr]
+            c.mask_cores = flat.ctypes.data_as(nat.c_double_p)
+            c.mask_ranks = rr.ctypes.data_as(nat.c_int_p)
+            c.mask_cap = cap
+        c.chi_max = chi_max
+        c.eps = eps
+        c.precision = precision
+        c.hadamard = hadamard
+        c.sweeps = sweeps
+        if modes is not None:
+            m = np.ascontiguousarray(modes, dtype=np.float64)
+            self._keep.append(m)
+            c.n_modes = m.shape[0]
+            c.modes = m.ctypes.data_as(nat.c_double_p)
+        self.cfg = c
+        self.n = n_per_axis
+        self.N = 1 << n_per_axis
+        self.L = 3 * n_per_axis
+        self.Q = lattice
+        self.chi = chi_max
+        h = ctypes.c_void_p()
+        nat.check(nat.lib().tnlbm_create(ctypes.byref(c), ctypes.byref(h)), "tnlbm_create")
+        self.h = h
+        self._keep = []
+
+    def step(self, k=1):
+        nat.check(nat.lib().tnlbm_step(self.h, k), "tnlbm_step")
+
+    def macroscopic(self):
+        N3 = self.N ** 3
+        rho = np.empty(N3)
+        u = np.empty(3 * N3)
+        nat.check(nat.lib().tnlbm_macroscopic(self.h, rho.ctypes.data_as(ctypes.c_void_p),
+                                              u.ctypes.data_as(ctypes.c_void_p)), "tnlbm_macroscopic")
+        N = self.N
+        return rho.reshape(N, N, N), u.reshape(3, N, N, N)
+
+    def get_populations(self):
+        ms = mps_size(self.L, self.chi)
+        cores = np.empty(self.Q * ms)
+        ranks = np.empty(self.Q * (self.L + 1), dtype=np.int32)
+        nat.check(nat.lib().tnlbm_get_populations(self.h, cores.ctypes.data_as(ctypes.c_void_p),
+                                                  ranks.ctypes.data_as(ctypes.c_void_p)), "get_populations")
+        out = []
+        for i in range(self.Q):
+            r = ranks[i * (self.L + 1):(i + 1) * (self.L + 1)]
+            cs = []
+            for k in range(self.L):
+                o = i * ms + mps_offset(self.L, self.chi, k)
+                cs.append(cores[o:o + r[k] * 2 * r[k + 1]].reshape(r[k], 2, r[k + 1]).copy())
+            out.append(cs)
+        return out
+
+    def set_populations(self, pops):
+        ms = mps_size(self.L, self.chi)
+        cores = np.zeros(self.Q * ms)
+        ranks = np.ones(self.Q * (self.L + 1), dtype=np.int32)
+        for i, cs in enumerate(pops):
+            for k, c in enumerate(cs):
+                o = i * ms + mps_offset(self.L, self.chi, k)
+                cores[o:o + c.size] = c.reshape(-1)
+                ranks[i * (self.L + 1) + k + 1] = c.shape[2]
+        nat.check(nat.lib().tnlbm_set_populations(self.h, cores.ctypes.data_as(ctypes.c_void_p),
+                                                  ranks.ctypes.data_as(ctypes.c_void_p)), "set_populations")
+
+    def step_timed(self, k=1):
+        """Device milliseconds of k graph launches (CUDA events)."""
+        ms = ctypes.c_double()
+        nat.check(nat.lib().tnlbm_step_timed(self.h, k, ctypes.byref(ms)), "tnlbm_step_timed")
+        return ms.value
+
+    def profile_step(self):
+        """One eager step; per kernel class: (ms, algorithmic flops, launches)."""
+        n = len(nat.KERNEL_CLASSES)
+        ms = (ctypes.c_double * n)()
+        fl = (ctypes.c_double * n)()
+        la = (ctypes.c_int * n)()
+        nat.check(nat.lib().tnlbm_profile_step(self.h, ms, fl, la), "tnlbm_profile_step")
+        return {c: dict(ms=ms[i], flops=fl[i], launches=la[i]) for i, c in enumerate(nat.KERNEL_CLASSES)}
+
+    def stats(self):
+        s = nat.Stats()
+        nat.check(nat.lib().tnlbm_stats_get(self.h, ctypes.byref(s)), "tnlbm_stats_get")
+        return {f: getattr(s, f) for f, _ in nat.Stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            nat.lib().tnlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
