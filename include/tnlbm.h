@@ -177,6 +177,24 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms,
                         int *const *dst_ranks, int dst_cap, int chi_max,
                         double eps, void *stream);
 
+/* Same result as tnlbm_lincomb_round, for callers that cannot allocate device
+ * memory at the point of the call: code whose device memory is entirely held
+ * by a pool allocator, and code that must not stall the device (cudaFree
+ * synchronises it).  The paper has no counterpart to this entry point.
+ * It calls no cudaMalloc / cudaFree: its workspace is a fixed 16 MiB array, a
+ * table of 64 jobs and 64 rank-1 masks in the library's static device memory,
+ * held by every GPU that loads the library until the process exits.  Requests
+ * that need more return TNLBM_E_ARG with a message.  All calls share these
+ * arrays (and fixed host staging tables): calls whose work overlaps on the GPU,
+ * or that come from several host threads at once, race.  The status word is
+ * cleared at the start of each call.  The first call on a device looks up the
+ * arrays' device addresses (cudaGetSymbolAddress) and should come before any
+ * stream capture that includes this call.  Synchronous on `stream`. */
+int tnlbm_lincomb_round_noalloc(int precision, int n_bits, int batch, int nterms,
+                                const tnlbm_term *terms, void *const *dst,
+                                int *const *dst_ranks, int dst_cap, int chi_max,
+                                double eps, void *stream);
+
 /* dst[b] = the single term, formed exactly without rounding (bond grows:
  * SHIFT doubles it inside the axis span, KRON multiplies bonds). */
 int tnlbm_materialize(int precision, int n_bits, int batch,

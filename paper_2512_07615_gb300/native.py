@@ -92,6 +92,10 @@ SIGNATURES = {
                                            ctypes.POINTER(Term), ctypes.POINTER(ctypes.c_void_p),
                                            ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
                                            ctypes.c_double, ctypes.c_void_p]),
+    "tnlbm_lincomb_round_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(Term), ctypes.POINTER(ctypes.c_void_p),
+                                                   ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_void_p]),
     "tnlbm_materialize": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Term),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.c_int, ctypes.c_void_p]),

@@ -126,6 +126,18 @@ def lincomb_round(batches, dst, chi_max, eps, stream=None):
     nat.check(rc, "tnlbm_lincomb_round")
 
 
+def lincomb_round_noalloc(batches, dst, chi_max, eps, stream=None):
+    """As lincomb_round, through the allocation-free entry point
+    (tnlbm_lincomb_round_noalloc): for callers that cannot allocate device
+    memory at the call; its workspace is the library's fixed static arrays."""
+    arr, nterms, keep = _terms_array(batches)
+    p = dst[0].precision
+    rc = nat.lib().tnlbm_lincomb_round_noalloc(p, dst[0].L // 3, len(dst), nterms, arr,
+                                               _ptrs([d.data for d in dst]), _ptrs([d.ranks for d in dst]),
+                                               dst[0].cap, chi_max, eps, _stream(stream))
+    nat.check(rc, "tnlbm_lincomb_round_noalloc")
+
+
 def materialize(terms, dst, stream=None):
     arr, _, keep = _terms_array([[t] for t in terms])
     p = dst[0].precision
