@@ -37,6 +37,10 @@ WORKLOADS = {
     "porous128": dict(n=7, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
                       chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
                       radius=10.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
+    # same chi and per-job matrix shapes as porous128 on 64^3 (for kernel captures)
+    "porous64": dict(n=6, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
+                     chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
+                     radius=5.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
     "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
                       chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
                       n_modes=0, mode_seed=0),
@@ -59,7 +63,8 @@ def make_sim(w, solid, modes):
     import paper_2512_07615_gb300 as tl
     return tl.Sim(w["n"], lattice=w["lattice"], tau=w["tau"], periodic=w["periodic"], solid=solid,
                   chi_mask=w["chi_mask"], eps_mask=w["eps_mask"], force=w["force"], chi_max=w["chi"],
-                  eps=w["eps"], precision=w["precision"], hadamard=0, sweeps=2, modes=modes)
+                  eps=w["eps"], precision=w["precision"], hadamard=0, sweeps=2, modes=modes,
+                  conserve_mass=w["precision"] == 1)
 
 
 class Clocks:
@@ -216,6 +221,7 @@ def main():
               "chi_max": w["chi"], "chi_mask": w["chi_mask"] if solid is not None else None,
               "eps": w["eps"], "tau": w["tau"], "products": "variational fit, 2 sweeps",
               "storage": "fp32" if w["precision"] == 1 else "fp64",
+              "mass_correction": w["precision"] == 1,
               "l2_flush": "working set > L2 (129 MB) is not claimed; each step touches ~GBs of environments"}
 
     if args.impl == "reference":
@@ -254,6 +260,8 @@ def main():
     t0 = time.time()
     sim = make_sim(w, solid, modes)
     setup_s = time.time() - t0
+    rho_start, _ = sim.macroscopic()
+    mass_start = float(rho_start.sum())
     sim.step(args.warmup)
 
     def barrier():
@@ -273,9 +281,12 @@ def main():
         ms = float(t.item())
     st = sim.stats()
     value = world * N3 * args.steps / (ms / 1e3) / 1e6
+    rho_end, _ = sim.macroscopic()
+    mass_drift = abs(float(rho_end.sum()) - mass_start) / mass_start
 
     # one profiled (eager, serialised) step: per kernel class time and FLOPs
     prof = sim.profile_step()
+    round_phases = prof["round"].pop("phase_cycles")
     total_prof_ms = sum(v["ms"] for v in prof.values())
     dom = max(prof, key=lambda c: prof[c]["ms"])
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
@@ -292,7 +303,11 @@ def main():
                 "share_of_profiled_step": prof[dom]["ms"] / total_prof_ms if total_prof_ms else None,
                 "classes": {c: {"ms": round(v["ms"], 3), "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12
                                                                     if v["ms"] > 0 else 0.0),
-                                "launches": v["launches"]} for c, v in prof.items()}}
+                                "launches": v["launches"]} for c, v in prof.items()},
+                "round_phase_share": {p: round(round_phases[p] / max(sum(round_phases[q] for q in
+                                      ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")), 1.0), 4)
+                                      for p in ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")},
+                "jacobi_sweeps_per_svd": round_phases["jacobi_sweeps"] / max(round_phases["svd_count"], 1.0)}
 
     # end to end through the C ABI: populations host -> device, step, device -> host
     e2e = None
@@ -326,6 +341,7 @@ def main():
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
+               "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out))
     sim.close()

@@ -87,6 +87,11 @@ typedef struct {
                               k.x/N + phase)), rounded once                     */
   const double *modes;     /* host [n_modes][8]: kx ky kz phase a_rho a_ux a_uy a_uz */
   int max_jobs_in_flight;  /* 0 = default; caps rounding CTAs per launch        */
+  int conserve_mass;       /* 1: after every step, rescale all populations by
+                              M0 / M (M = sum_i <f_i, 1> in FP64, M0 its value
+                              at the start): removes the ~1e-6-per-step mass
+                              drift of FP32 core storage.  Not part of the
+                              paper's method; default 0                         */
 } tnlbm_config;
 
 typedef struct {
@@ -132,8 +137,11 @@ enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_
 /* Advance one step with eager (non-graph), serialised launches and report per
  * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
  * launch), algorithmic FLOPs flops[] (counted on the device from the realised
- * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[]. */
-int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches);
+ * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[].
+ * phases (nullable, 8 doubles): SM cycles of the rounding kernel's phases
+ * summed over its jobs: term formation, R*W product, QR, Jacobi, SVD outputs,
+ * Q*US product (indices 0..5). */
+int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches, double *phases);
 int tnlbm_destroy(tnlbm_sim *s); /* NULL-safe */
 const char *tnlbm_last_error(void);
 

@@ -147,6 +147,8 @@ struct tnlbm_sim {
   MpsRef* d_rho_ref = nullptr;
   MpsRef* d_copy_src = nullptr;
   MpsRef* d_copy_dst = nullptr;
+  double* d_mass = nullptr;      // [Q] per-population masses (mass correction)
+  double* d_mass0 = nullptr;     // initial total mass
   int launches_per_step = 0;
   int64_t steps = 0;
   int pending_status = 0;
@@ -482,6 +484,11 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
       cudaStreamWaitEvent(s->s0, s->ev_join, 0);
     }
   }
+  if (s->cfg.conserve_mass) {
+    launch_mass_fix<T>(s->d_copy_src, s->lat.Q, s->L, s->d_mass, s->d_mass0, s->s0);
+    if (prof) prof->mark(C_COPY);
+    n += 2;
+  }
   launch_copy<T>(s->d_copy_src, s->d_copy_dst, s->lat.Q, s->L, s->s0);
   if (prof) prof->mark(C_COPY);
   ++n;
@@ -676,6 +683,23 @@ static int create_impl(tnlbm_sim* s) {
   }
   int rc = upload_levels<T>(s);
   if (rc) return rc;
+  // initial mass, for the optional mass correction
+  s->d_mass = (double*)s->arena.alloc(Q * sizeof(double));
+  s->d_mass0 = (double*)s->arena.alloc(sizeof(double));
+  if (!s->d_mass || !s->d_mass0) return TNLBM_E_OOM;
+  {
+    MpsRef* dref = (MpsRef*)s->arena.alloc(Q * sizeof(MpsRef));
+    std::vector<MpsRef> refs;
+    for (int i = 0; i < Q; ++i) refs.push_back(s->nodes[s->f_state[i]]);
+    cudaMemcpy(dref, refs.data(), Q * sizeof(MpsRef), cudaMemcpyHostToDevice);
+    launch_inner_ones<T>(dref, Q, s->L, s->d_mass, s->s0);
+    std::vector<double> hm(Q);
+    cudaMemcpyAsync(hm.data(), s->d_mass, Q * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+    TN_CUDA(cudaStreamSynchronize(s->s0));
+    double m0 = 0.0;
+    for (double v : hm) m0 += v;
+    cudaMemcpy(s->d_mass0, &m0, sizeof(double), cudaMemcpyHostToDevice);
+  }
   // capture one step as a graph
   TN_CUDA(cudaStreamSynchronize(s->s0));
   TN_CUDA(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
@@ -762,26 +786,24 @@ template <typename T>
 static int macro_impl(tnlbm_sim* s, double* rho, double* u) {
   using namespace tn;
   const size_t nc = (size_t)s->N * s->N * s->N;
-  double *d = nullptr, *dm = nullptr;
-  T* tmp = nullptr;
+  double *d = nullptr, *dm = nullptr, *tmp = nullptr;
   void* scr = nullptr;
   const int capmax = std::max(s->cfg.chi_max, s->mask_node >= 0 ? s->nodes[s->mask_node].cap : 1);
   const size_t sb = contract_scratch_bytes(s->n, capmax, sizeof(T));
   auto fin = [&](int rc) { cudaFree(d); cudaFree(dm); cudaFree(tmp); cudaFree(scr); return rc; };
-  if (cudaMalloc(&d, 4 * nc * sizeof(double)) != cudaSuccess || cudaMalloc(&tmp, nc * sizeof(T)) != cudaSuccess ||
+  if (cudaMalloc(&d, 4 * nc * sizeof(double)) != cudaSuccess || cudaMalloc(&tmp, nc * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&scr, sb) != cudaSuccess) {
     set_error("out of device memory in tnlbm_macroscopic");
     return fin(TNLBM_E_OOM);
   }
   double *dr = d, *jx = d + nc, *jy = d + 2 * nc, *jz = d + 3 * nc;
   for (int i = 0; i < s->lat.Q; ++i) {
-    contract_dense<T>(s->nodes[s->f_state[i]], s->n, tmp, scr, sb, s->s0);
-    launch_accum_moments<T>(tmp, nc, dr, jx, jy, jz, s->lat.c[i][0], s->lat.c[i][1], s->lat.c[i][2], i == 0, s->s0);
+    contract_dense_f64<T>(s->nodes[s->f_state[i]], s->n, tmp, scr, sb, s->s0);
+    launch_accum_moments<double>(tmp, nc, dr, jx, jy, jz, s->lat.c[i][0], s->lat.c[i][1], s->lat.c[i][2], i == 0, s->s0);
   }
   if (s->mask_node >= 0) {
     if (cudaMalloc(&dm, nc * sizeof(double)) != cudaSuccess) return fin(TNLBM_E_OOM);
-    contract_dense<T>(s->nodes[s->mask_node], s->n, tmp, scr, sb, s->s0);
-    launch_cast_double<T>(tmp, nc, dm, s->s0);
+    contract_dense_f64<T>(s->nodes[s->mask_node], s->n, dm, scr, sb, s->s0);
   }
   if (u) launch_velocity(nc, dr, jx, jy, jz, dm, s->cfg.force[0], s->cfg.force[1], s->cfg.force[2], s->s0);
   if (rho) cudaMemcpyAsync(rho, dr, nc * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
@@ -1122,11 +1144,11 @@ int tnlbm_from_dense(int precision, int n_bits, const void* dense, void* dst, in
 
 // ================================================================ measurement
 template <typename T>
-static int profile_impl(tnlbm_sim* s, double* ms, double* flops, int* launches) {
+static int profile_impl(tnlbm_sim* s, double* ms, double* flops, int* launches, double* phases) {
   using namespace tn;
   double* d_ctr = nullptr;
-  TN_CUDA(cudaMalloc(&d_ctr, C_COUNT * sizeof(double)));
-  cudaMemsetAsync(d_ctr, 0, C_COUNT * sizeof(double), s->s0);
+  TN_CUDA(cudaMalloc(&d_ctr, CTR_SIZE * sizeof(double)));
+  cudaMemsetAsync(d_ctr, 0, CTR_SIZE * sizeof(double), s->s0);
   Prof prof;
   prof.st = s->s0;
   prof.d_ctr = d_ctr;
@@ -1137,7 +1159,11 @@ static int profile_impl(tnlbm_sim* s, double* ms, double* flops, int* launches) 
   if (e != cudaSuccess) { cudaFree(d_ctr); return cuda_fail(e, "tnlbm_profile_step"); }
   for (int c = 0; c < C_COUNT; ++c) { ms[c] = 0.0; launches[c] = 0; }
   prof.collect(ms, launches);
-  cudaMemcpy(flops, d_ctr, C_COUNT * sizeof(double), cudaMemcpyDeviceToHost);
+  double h_ctr[CTR_SIZE];
+  cudaMemcpy(h_ctr, d_ctr, sizeof(h_ctr), cudaMemcpyDeviceToHost);
+  for (int c = 0; c < C_COUNT; ++c) flops[c] = h_ctr[c];
+  if (phases)
+    for (int p = 0; p < PH_COUNT; ++p) phases[p] = h_ctr[C_COUNT + p];
   cudaFree(d_ctr);
   s->steps += 1;
   int st[STATUS_INTS] = {0};
@@ -1169,10 +1195,10 @@ int tnlbm_step_timed(tnlbm_sim* s, int k, double* ms) {
   return 0;
 }
 
-int tnlbm_profile_step(tnlbm_sim* s, double* ms, double* flops, int* launches) {
+int tnlbm_profile_step(tnlbm_sim* s, double* ms, double* flops, int* launches, double* phases) {
   if (!s || !ms || !flops || !launches) { set_error("bad arguments to tnlbm_profile_step"); return TNLBM_E_ARG; }
-  return s->prec == TNLBM_FP64 ? profile_impl<double>(s, ms, flops, launches)
-                               : profile_impl<float>(s, ms, flops, launches);
+  return s->prec == TNLBM_FP64 ? profile_impl<double>(s, ms, flops, launches, phases)
+                               : profile_impl<float>(s, ms, flops, launches, phases);
 }
 
 }  // extern "C"

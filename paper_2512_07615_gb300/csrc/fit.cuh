@@ -68,6 +68,12 @@ enum ScalSlot : int { SC_NEG_RHO0 = 0, SC_INV1 = 1, SC_INV2 = 2, SC_INV3 = 3, SC
 template <typename T>
 void launch_rho0(const MpsRef* d_rho, int L, double n_fluid, double* d_scal, cudaStream_t st);
 
+// Mass correction: mass[i] = <X_i, 1> for the n MPS (one CTA each), then every
+// X_i's core 0 is scaled by mass0[0] / sum_i mass[i].
+template <typename T>
+void launch_mass_fix(const MpsRef* d_refs, int n, int L, double* d_mass, const double* d_mass0,
+                     cudaStream_t st);
+
 // copy MPS src[b] -> dst[b] (cores and bonds)
 template <typename T>
 void launch_copy(const MpsRef* d_src, const MpsRef* d_dst, int n, int L, cudaStream_t st);
@@ -77,6 +83,9 @@ template <typename T>
 int contract_dense(const MpsRef& X, int n_bits, T* d_dense, void* d_scratch, size_t scratch_bytes,
                    cudaStream_t st);
 size_t contract_scratch_bytes(int n_bits, int cap, size_t elem);
+template <typename T>
+int contract_dense_f64(const MpsRef& X, int n_bits, double* d_dense, void* d_scratch, size_t scratch_bytes,
+                       cudaStream_t st);
 
 // accumulate rho += f, j += c f (double) from a dense population
 template <typename T>

@@ -254,19 +254,28 @@ __device__ void cta_gemm(int M, int N, int K, const T* A, int lda, const T* B, i
 template <typename T>
 __device__ void householder_qr_par(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
                                    double* tau, T* wv, double* red) {
-  // all arithmetic in T: on GB300 FP64 runs at ~1/64 of the FP32 rate
+  // All arithmetic in T: on GB300 FP64 runs at ~1/64 of the FP32 rate.
+  // Per column: one reduction for the norm (fused into the previous update),
+  // one pass for the reflector inner products (the reflector is kept unscaled
+  // and its scale folded in), one pass for the rank-1 update that also stores
+  // the scaled reflector.  Three barriers per column.
   const int kk = imin(m, n);
   const int G = 8;                                 // threads per column in the dot phase
-  __shared__ T s_scale;
+  __shared__ T s_scale, s_norm2;
   T* redT = (T*)red;
-  for (int j = 0; j < kk; ++j) {
+  // norm of column 0 below the diagonal
+  {
     T part = (T)0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-      const T v = A[(size_t)i * lda + j];
+    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
+      const T v = A[(size_t)i * lda];
       part += v * v;
     }
-    const T sig2 = block_sum_t<T>(part, redT);
+    const T t = block_sum_t<T>(part, redT);
+    if (threadIdx.x == 0) s_norm2 = t;
+  }
+  for (int j = 0; j < kk; ++j) {
     if (threadIdx.x == 0) {
+      const T sig2 = s_norm2;
       const T alpha = A[(size_t)j * lda + j];
       if (sig2 == (T)0) {
         tau[j] = 0.0;
@@ -280,35 +289,48 @@ __device__ void householder_qr_par(T* A, int m, int n, int lda, T* Q, int ldq, T
     }
     __syncthreads();
     const T tj = (T)tau[j];
-    if (tj == (T)0) continue;                       // uniform across the block
     const T sc = s_scale;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
-    __syncthreads();
-    // w_c = A[j][c] + sum_{i>j} v_i A[i][c], c > j
     const int nc = n - j - 1;
-    // loop bounds uniform over the block so every warp shuffles with all lanes
-    for (int base = 0; base < nc * G; base += blockDim.x) {
-      const int t = base + threadIdx.x;
-      const bool act = t < nc * G;
-      const int c = j + 1 + t / G, p = t % G;
-      T acc = (T)0;
-      if (act) {
-        if (p == 0) acc = A[(size_t)j * lda + c];
-        for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
-      }
+    if (tj != (T)0) {
+      // w_c = (A[j][c] + sc * sum_{i>j} A[i][j] A[i][c]) * tau, c > j
+      for (int base = 0; base < nc * G; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const bool act = t < nc * G;
+        const int c = j + 1 + t / G, p = t % G;
+        T acc = (T)0;
+        if (act)
+          for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-      if (act && p == 0) wv[c] = acc * tj;
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+        if (act && p == 0) wv[c] = (A[(size_t)j * lda + c] + sc * acc) * tj;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // A[i][c] -= w_c v_i (v_j = 1)
+    // A[i][c] -= w_c v_i with v_i = sc A[i][j] (v_j = 1); store v; norm of column j+1
     const int rows = m - j;
-    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
-      const int ii = j + t / nc, c = j + 1 + t % nc;
-      const T vi = (ii == j) ? (T)1 : A[(size_t)ii * lda + j];
-      A[(size_t)ii * lda + c] -= wv[c] * vi;
+    T part = (T)0;
+    if (tj != (T)0) {
+      for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+        const int ii = j + t / nc, c = j + 1 + t % nc;
+        const T vi = (ii == j) ? (T)1 : sc * A[(size_t)ii * lda + j];
+        const T nv = A[(size_t)ii * lda + c] - wv[c] * vi;
+        A[(size_t)ii * lda + c] = nv;
+        if (c == j + 1 && ii > j + 1) part += nv * nv;
+      }
+      __syncthreads();
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
+    } else if (nc > 0) {
+      for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) {
+        const T v = A[(size_t)i * lda + j + 1];
+        part += v * v;
+      }
     }
-    __syncthreads();
+    if (j + 1 < kk) {
+      const T t = block_sum_t<T>(part, redT);
+      if (threadIdx.x == 0) s_norm2 = t;
+    } else {
+      __syncthreads();
+    }
   }
   // R with non-negative diagonal
   for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {

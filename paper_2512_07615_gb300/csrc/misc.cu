@@ -66,6 +66,29 @@ void launch_rho0(const MpsRef* d_rho, int L, double n_fluid, double* d_scal, cud
   rho0_kernel<T><<<1, 256, 0, st>>>(d_rho, L, n_fluid, d_scal);
 }
 
+// ---------------------------------------------------------------- mass correction
+template <typename T>
+__global__ void mass_scale_kernel(const MpsRef* refs, int n, const double* mass, const double* mass0) {
+  __shared__ double fac;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m += mass[i];
+    fac = (m != 0.0 && isfinite(m)) ? mass0[0] / m : 1.0;
+  }
+  __syncthreads();
+  const MpsRef& X = refs[blockIdx.x];
+  const int r1 = X.ranks[1];
+  T* c0 = (T*)X.base;                        // core 0 is 1 x 2 x r1
+  for (int i = threadIdx.x; i < 2 * r1; i += blockDim.x) c0[i] = (T)((double)c0[i] * fac);
+}
+
+template <typename T>
+void launch_mass_fix(const MpsRef* d_refs, int n, int L, double* d_mass, const double* d_mass0,
+                     cudaStream_t st) {
+  inner_ones_kernel<T><<<n, 256, 0, st>>>(d_refs, L, d_mass);
+  mass_scale_kernel<T><<<n, 64, 0, st>>>(d_refs, n, d_mass, d_mass0);
+}
+
 // ---------------------------------------------------------------- copies
 template <typename T>
 __global__ void copy_kernel(const MpsRef* src, const MpsRef* dst, int L) {
@@ -95,18 +118,21 @@ __host__ __device__ inline size_t site_index(int x, int y, int z, int n) {
   return idx;
 }
 
+// Output contractions accumulate in FP64 whatever the storage type: they run
+// once per output, not on the hot path, and FP32 products of L cores would
+// bias sums over the lattice at the 1e-6 level.
 template <typename T>
-__global__ void left_rows_kernel(MpsRef X, int L, int h, T* Lm, int ldl) {
-  __shared__ T v[1024], w[1024];
+__global__ void left_rows_kernel(MpsRef X, int L, int h, double* Lm, int ldl) {
+  __shared__ double v[1024], w[1024];
   const size_t l = blockIdx.x;
   for (int k = 0; k < h; ++k) {
     const int s = (int)((l >> (h - 1 - k)) & 1);
     const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
     const T* A = (const T*)X.base + core_offset(L, X.cap, k);
     for (int j = threadIdx.x; j < r1; j += blockDim.x) {
-      T acc = (T)0;
-      if (k == 0) acc = A[(size_t)s * r1 + j];
-      else for (int i = 0; i < r0; ++i) acc += v[i] * A[((size_t)i * 2 + s) * r1 + j];
+      double acc = 0.0;
+      if (k == 0) acc = (double)A[(size_t)s * r1 + j];
+      else for (int i = 0; i < r0; ++i) acc += v[i] * (double)A[((size_t)i * 2 + s) * r1 + j];
       w[j] = acc;
     }
     __syncthreads();
@@ -118,17 +144,17 @@ __global__ void left_rows_kernel(MpsRef X, int L, int h, T* Lm, int ldl) {
 }
 
 template <typename T>
-__global__ void right_cols_kernel(MpsRef X, int L, int h, T* Rt, int ldr) {
-  __shared__ T v[1024], w[1024];
+__global__ void right_cols_kernel(MpsRef X, int L, int h, double* Rt, int ldr) {
+  __shared__ double v[1024], w[1024];
   const size_t q = blockIdx.x;
   for (int k = L - 1; k >= h; --k) {
     const int s = (int)((q >> (L - 1 - k)) & 1);
     const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
     const T* A = (const T*)X.base + core_offset(L, X.cap, k);
     for (int i = threadIdx.x; i < r0; i += blockDim.x) {
-      T acc = (T)0;
-      if (k == L - 1) acc = A[(size_t)i * 2 + s];
-      else for (int j = 0; j < r1; ++j) acc += A[((size_t)i * 2 + s) * r1 + j] * v[j];
+      double acc = 0.0;
+      if (k == L - 1) acc = (double)A[(size_t)i * 2 + s];
+      else for (int j = 0; j < r1; ++j) acc += (double)A[((size_t)i * 2 + s) * r1 + j] * v[j];
       w[i] = acc;
     }
     __syncthreads();
@@ -140,7 +166,7 @@ __global__ void right_cols_kernel(MpsRef X, int L, int h, T* Rt, int ldr) {
 }
 
 template <typename T>
-__global__ void join_kernel(MpsRef X, int n, int h, const T* Lm, const T* Rt, int ld, T* out) {
+__global__ void join_kernel(MpsRef X, int n, int h, const double* Lm, const double* Rt, int ld, T* out) {
   const int L = 3 * n;
   const size_t N = (size_t)1 << n;
   const size_t total = N * N * N;
@@ -150,32 +176,45 @@ __global__ void join_kernel(MpsRef X, int n, int h, const T* Lm, const T* Rt, in
     const int z = (int)(idx % N), y = (int)((idx / N) % N), x = (int)(idx / (N * N));
     const size_t si = site_index(x, y, z, n);
     const size_t l = si >> (L - h), q = si & (((size_t)1 << (L - h)) - 1);
-    const T* a = Lm + l * ld;
-    const T* b = Rt + q * ld;
-    T acc = (T)0;
+    const double* a = Lm + l * ld;
+    const double* b = Rt + q * ld;
+    double acc = 0.0;
     for (int j = 0; j < rh; ++j) acc += a[j] * b[j];
-    out[idx] = acc;
+    out[idx] = (T)acc;
   }
 }
 
 size_t contract_scratch_bytes(int n_bits, int cap, size_t elem) {
   const int L = 3 * n_bits, h = L / 2;
   const size_t ld = bond_cap(L, cap, h);
-  return (((size_t)1 << h) + ((size_t)1 << (L - h))) * ld * elem;
+  (void)elem;
+  return (((size_t)1 << h) + ((size_t)1 << (L - h))) * ld * sizeof(double);
+}
+
+template <typename T, typename OutT>
+int contract_dense_to(const MpsRef& X, int n_bits, OutT* d_dense, void* d_scratch, size_t scratch_bytes,
+                      cudaStream_t st) {
+  const int L = 3 * n_bits, h = L / 2;
+  const int ld = bond_cap(L, X.cap, h);
+  if (contract_scratch_bytes(n_bits, X.cap, sizeof(T)) > scratch_bytes) return TNLBM_E_ARG;
+  double* Lm = (double*)d_scratch;
+  double* Rt = Lm + ((size_t)1 << h) * ld;
+  left_rows_kernel<T><<<(unsigned)(1u << h), 256, 0, st>>>(X, L, h, Lm, ld);
+  right_cols_kernel<T><<<(unsigned)(1u << (L - h)), 256, 0, st>>>(X, L, h, Rt, ld);
+  join_kernel<OutT><<<152 * 16, 256, 0, st>>>(X, n_bits, h, Lm, Rt, ld, d_dense);
+  return 0;
 }
 
 template <typename T>
 int contract_dense(const MpsRef& X, int n_bits, T* d_dense, void* d_scratch, size_t scratch_bytes,
                    cudaStream_t st) {
-  const int L = 3 * n_bits, h = L / 2;
-  const int ld = bond_cap(L, X.cap, h);
-  if (contract_scratch_bytes(n_bits, X.cap, sizeof(T)) > scratch_bytes) return TNLBM_E_ARG;
-  T* Lm = (T*)d_scratch;
-  T* Rt = Lm + ((size_t)1 << h) * ld;
-  left_rows_kernel<T><<<(unsigned)(1u << h), 256, 0, st>>>(X, L, h, Lm, ld);
-  right_cols_kernel<T><<<(unsigned)(1u << (L - h)), 256, 0, st>>>(X, L, h, Rt, ld);
-  join_kernel<T><<<152 * 16, 256, 0, st>>>(X, n_bits, h, Lm, Rt, ld, d_dense);
-  return 0;
+  return contract_dense_to<T, T>(X, n_bits, d_dense, d_scratch, scratch_bytes, st);
+}
+
+template <typename T>
+int contract_dense_f64(const MpsRef& X, int n_bits, double* d_dense, void* d_scratch, size_t scratch_bytes,
+                       cudaStream_t st) {
+  return contract_dense_to<T, double>(X, n_bits, d_dense, d_scratch, scratch_bytes, st);
 }
 
 template <typename T>
@@ -398,7 +437,9 @@ int tt_svd_dense(const T* d_dense, int n, T* d_dst, int* d_dst_ranks, int dst_ca
   template void launch_inner_ones<T>(const MpsRef*, int, int, double*, cudaStream_t);           \
   template void launch_rho0<T>(const MpsRef*, int, double, double*, cudaStream_t);              \
   template void launch_copy<T>(const MpsRef*, const MpsRef*, int, int, cudaStream_t);           \
+  template void launch_mass_fix<T>(const MpsRef*, int, int, double*, const double*, cudaStream_t); \
   template int contract_dense<T>(const MpsRef&, int, T*, void*, size_t, cudaStream_t);          \
+  template int contract_dense_f64<T>(const MpsRef&, int, double*, void*, size_t, cudaStream_t);  \
   template void launch_accum_moments<T>(const T*, size_t, double*, double*, double*, double*,   \
                                         int, int, int, int, cudaStream_t);                       \
   template int tt_svd_dense<T>(const T*, int, T*, int*, int, int, double, int*, cudaStream_t); \

@@ -168,6 +168,20 @@ static constexpr int SM_WV = SM_SIG + MAXK * 8;
 static_assert(SM_WV + MAXK * 8 <= SM_SMALL, "bookkeeping overlaps the work area");
 static_assert(16 * 1024 >= (2 * TN_MAXT * (TN_MAXL + 1) + TN_MAXT + 2 * (TN_MAXL + 1) + MAXK) * 4, "bond tables");
 
+// phase timer of thread 0 (profiling only)
+struct PhaseClock {
+  long long t0 = 0;
+  double acc[PH_COUNT] = {0};
+  bool on;
+  __device__ explicit PhaseClock(bool enable) : on(enable && threadIdx.x == 0) { if (on) t0 = clock64(); }
+  __device__ void lap(int ph) {
+    if (!on) return;
+    const long long t = clock64();
+    acc[ph] += (double)(t - t0);
+    t0 = t;
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L,
                                                    int n_bits, const T* __restrict__ masks,
@@ -193,6 +207,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
   const int nt = J.nterms;
   T* scr = (T*)J.scratch;
   double flops = 0.0;                                  // thread 0 only
+  PhaseClock pc(ctr != nullptr);
   if (threadIdx.x == 0) s_bad = 0;
   __syncthreads();
   // ---- bonds of every term and of the wide sum
@@ -273,6 +288,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
       }
     }
     __syncthreads();
+    pc.lap(PH_TERMS);
     // (b) M = Rc * blockdiag(W): rows (r, s), row length Rk1, leading dim ld
     const int mrows = 2 * rc;
     int ld = Rk1 | 1;
@@ -291,6 +307,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
         cta_gemm<T>(rc, r1, r0, Rc + ro, Rk, Wt + s * r1, 2 * r1, M + (size_t)s * ld + co, 2 * ld, last);
       if (threadIdx.x == 0) flops += 4.0 * rc * r0 * r1;
     }
+    pc.lap(PH_GEMM_M);
     T* Qk = scr + J.lay.q_off[k];
     if (last) {
       for (int idx = threadIdx.x; idx < mrows; idx += blockDim.x) Qk[idx] = M[(size_t)idx * ld];
@@ -302,6 +319,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     if (rq > MAXK || Rk1 > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
     householder_qr_par<T>(M, mrows, Rk1, ld, Qk, rq, Rc, Rk1, s_tau, s_wv, s_red);
     if (threadIdx.x == 0) flops += qr_flops(mrows, Rk1);
+    pc.lap(PH_QR);
     rc = rq;
     if (threadIdx.x == 0) s_q[k + 1] = rq;
     __syncthreads();
@@ -363,7 +381,10 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     }
     __syncthreads();
     const int maxsw = 60;
+    pc.lap(PH_SVD_OUT);
     int sw = jacobi_cols_hw<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
+    pc.lap(PH_JACOBI);
+    if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }   // sweeps, SVD count
     if (sw >= maxsw && threadIdx.x == 0) {
       flag(status, ST_NOCONV);
       if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big
@@ -434,8 +455,10 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     // C' = Q_{k-1} (2 q_{k-1} x m) * US (m x r)
     const int rows = 2 * s_q[k - 1];
     const T* Qp = scr + J.lay.q_off[k - 1];
+    pc.lap(PH_SVD_OUT);
     cta_gemm<T>(rows, r, m, Qp, m, US, r, C, r, false);
     if (threadIdx.x == 0) flops += 2.0 * rows * m * r;
+    pc.lap(PH_GEMM_C);
     rnext = r;
   }
   // core 0 = C (1 x 2 x r_1)
@@ -445,7 +468,10 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     if (threadIdx.x == 0) {
       J.dst.ranks[0] = 1;
       J.dst.ranks[L] = 1;
-      if (ctr) atomicAdd(&ctr[C_ROUND], flops);
+      if (ctr) {
+        atomicAdd(&ctr[C_ROUND], flops);
+        for (int p = 0; p < PH_COUNT; ++p) atomicAdd(&ctr[C_COUNT + p], pc.acc[p]);
+      }
     }
   }
 }

@@ -13,6 +13,7 @@ D3Q19, D3Q15 = 19, 15
 HADAMARD_FIT, HADAMARD_EXACT = 0, 1
 TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy")
+ROUND_PHASES = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus", "jacobi_sweeps", "svd_count")
 
 c_int_p = ctypes.POINTER(ctypes.c_int)
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -39,6 +40,7 @@ class Config(ctypes.Structure):
         ("n_modes", ctypes.c_int),
         ("modes", c_double_p),
         ("max_jobs_in_flight", ctypes.c_int),
+        ("conserve_mass", ctypes.c_int),
     ]
 
 
@@ -84,7 +86,7 @@ SIGNATURES = {
     "tnlbm_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "tnlbm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tnlbm_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
-    "tnlbm_profile_step": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_int_p]),
+    "tnlbm_profile_step": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_int_p, c_double_p]),
     "tnlbm_last_error": (ctypes.c_char_p, []),
     "tnlbm_mps_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
     "tnlbm_mps_offset": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),

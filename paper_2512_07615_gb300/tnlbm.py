@@ -192,7 +192,8 @@ class Sim:
 
     def __init__(self, n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
                  chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
-                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None):
+                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
+                 conserve_mass=False):
         c = nat.Config()
         c.n_per_axis = n_per_axis
         c.lattice = lattice
@@ -225,6 +226,7 @@ class Sim:
         c.precision = precision
         c.hadamard = hadamard
         c.sweeps = sweeps
+        c.conserve_mass = int(bool(conserve_mass))
         if modes is not None:
             m = np.ascontiguousarray(modes, dtype=np.float64)
             self._keep.append(m)
@@ -293,8 +295,11 @@ class Sim:
         ms = (ctypes.c_double * n)()
         fl = (ctypes.c_double * n)()
         la = (ctypes.c_int * n)()
-        nat.check(nat.lib().tnlbm_profile_step(self.h, ms, fl, la), "tnlbm_profile_step")
-        return {c: dict(ms=ms[i], flops=fl[i], launches=la[i]) for i, c in enumerate(nat.KERNEL_CLASSES)}
+        ph = (ctypes.c_double * 8)()
+        nat.check(nat.lib().tnlbm_profile_step(self.h, ms, fl, la, ph), "tnlbm_profile_step")
+        out = {c: dict(ms=ms[i], flops=fl[i], launches=la[i]) for i, c in enumerate(nat.KERNEL_CLASSES)}
+        out["round"]["phase_cycles"] = {p: ph[i] for i, p in enumerate(nat.ROUND_PHASES)}
+        return out
 
     def stats(self):
         s = nat.Stats()
