@@ -49,3 +49,8 @@ def random_mps(L, ranks, seed, scale=None):
 def feasible_ranks(L, chi):
     """Bond dimensions min(chi, 2**k, 2**(L-k)) of a generic MPS of L binary sites."""
     return [min(chi, 2 ** k, 2 ** (L - k)) for k in range(L + 1)]
+
+
+def gaussian_matrix(rows, cols, seed):
+    """Fixed standard normal test matrix of the randomized range finder."""
+    return np.random.default_rng(seed).standard_normal((rows, cols))

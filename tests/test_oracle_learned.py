@@ -1,0 +1,79 @@
+"""Pins of the learned-rank pieces of the oracle: MLP gradients against
+finite differences; the randomized truncation against the full SVD where the
+sample covers the spectrum, and its certificate rejecting samples that miss."""
+import numpy as np
+
+import synth
+from oracle import learned as LR
+from oracle import mps as M
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(0)
+    P = LR.mlp_init(3)
+    X = rng.standard_normal((7, LR.N_FEAT))
+    y = rng.uniform(0, 1, 7)
+    loss, g = LR.mlp_loss_grad(P, X, y)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        flat = P[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            h = 1e-6
+            old = flat[idx]
+            flat[idx] = old + h
+            lp, _ = LR.mlp_loss_grad(P, X, y)
+            flat[idx] = old - h
+            lm, _ = LR.mlp_loss_grad(P, X, y)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[name].reshape(-1)[idx]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def _mat(m, n, s, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, len(s))))
+    V, _ = np.linalg.qr(rng.standard_normal((n, len(s))))
+    return (U * s) @ V.T
+
+
+def test_rsvd_full_sample_equals_svd():
+    C = _mat(20, 12, np.linspace(3, 0.1, 12), 1)
+    omega = synth.gaussian_matrix(64, 64, 5)
+    ok, r, US, Vt, err2, res2 = LR.rsvd_truncate(C, 12, omega, 6, 0.0)
+    U, S, Wt = np.linalg.svd(C, full_matrices=False)
+    ref = (U[:, :6] * S[:6]) @ Wt[:6]
+    assert ok and r == 6 and res2 < 1e-20
+    np.testing.assert_allclose(US @ Vt, ref, atol=1e-12)
+    assert abs(err2 - np.sum(S[6:] ** 2)) < 1e-12
+
+
+def test_rsvd_gap_accepted_and_certificate_rejects_misses():
+    s = np.concatenate([np.linspace(2, 1, 5), 1e-6 * 0.5 ** np.arange(25)])
+    C = _mat(40, 40, s, 2)
+    omega = synth.gaussian_matrix(64, 64, 6)
+    ok, r, US, Vt, err2, res2 = LR.rsvd_truncate(C, 5, omega, 5, 0.0)
+    assert ok and r == 5
+    U, S, Wt = np.linalg.svd(C)
+    np.testing.assert_allclose(US @ Vt, (U[:, :5] * S[:5]) @ Wt[:5], atol=1e-9)
+    flat = _mat(40, 40, np.ones(40), 3)                  # no decay: a small sample misses mass
+    ok, r, *_ = LR.rsvd_truncate(flat, 5, omega, 30, 0.0, p=2)
+    assert not ok
+
+
+def test_round_learned_without_targets_is_round():
+    L = 9
+    A = M.add(synth.random_mps(L, synth.feasible_ranks(L, 5), 1), synth.random_mps(L, synth.feasible_ranks(L, 4), 2))
+    omega = synth.gaussian_matrix(128, 128, 7)
+    a, na, nf = LR.round_mps_learned(A, 6, 1e-12, None, omega)
+    b = M.round_mps(A, 6, 1e-12)
+    np.testing.assert_allclose(M.to_tensor(a), M.to_tensor(b), atol=1e-12)
+    # generous targets: every bond accepted, same tensor
+    c, na, nf = LR.round_mps_learned(A, 64, 0.0, [None] + [16] * (L - 1), omega)
+    assert na == L - 1 and nf == 0
+    np.testing.assert_allclose(M.to_tensor(c), M.to_tensor(A), atol=1e-12)
+
+
+def test_spectrum_features():
+    f = LR.spectrum_features(np.array([4.0, 2.0, 0.4]), 3, 12, 500)
+    assert f.shape == (18,)
+    np.testing.assert_allclose(f[:3], [0.0, np.log10(0.5), np.log10(0.1)])
+    assert f[3] == -20.0 and f[16] == 0.25 and f[17] == 0.5
