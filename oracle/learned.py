@@ -5,17 +5,20 @@ Neither part is in the paper; they replace the full SVD of the rounding sweep
 (Eq. svd-move) where that is safe.
 
 Randomized truncation of the centre matrix C (m x n) at target rank k:
-  l = min(max(k + p, l_min), m, n);  Y = C Omega[:n, :l];  Q = qr(Y);  B = Q^T C;
-  B = U S V^T;  the candidate rank r follows the usual rule applied to the
-  true errors:  err(r)^2 = ||C - Q B||^2 + sum_{j >= r} s_j^2.
-Because the singular values of Q B interlace below those of C,
-err(r)^2 <= opt(r)^2 + ||C - Q B||^2 with opt the optimal rank-r error, so the
-result is accepted when ||C - Q B||^2 <= eta * err(r)^2 (and the rank rule is
-satisfied inside the sample); otherwise the full SVD is used.  A spectrum with
-a flat tail beyond the sample cannot be certified this way and falls back.  Omega is a fixed
-Gaussian matrix passed in (drawn by synth).  The sample has at least
-l_min = 16 columns so that the spectrum it yields carries the 16 values the
-rank model reads at the next step.
+  l = min(max(k + p, l_min), m, n);  Y = C Omega[:n, :l];
+  q power steps (each: Q = qr(Y); Z = qr(C^T Q); Y = C Z);
+  Q = qr(Y);  B = Q^T C;  B = U S V^T;  the candidate rank r follows the usual
+  rule applied to the true errors:  err(r)^2 = ||C - Q B||^2 + sum_{j >= r} s_j^2.
+Since C^T C = B^T B + E^T E with E = C - Q B (Q^T E = 0), Ky Fan's inequality
+bounds the optimal rank-r error from below by err(r)^2 - ||E||^2, so
+||E||^2 <= eta err(r)^2 proves err(r)^2 <= opt(r)^2 / (1 - eta).  The result is
+accepted when the rank rule is met inside the sample and either the measured
+error is within the tolerance (err(r) <= delta) or, at the chi_max cap, the
+near-optimality bound above holds; otherwise the full SVD is used.  A spectrum
+with a flat tail beyond the sample cannot be certified this way and falls
+back.  Omega is a fixed Gaussian matrix passed in (drawn by synth).  The
+sample has at least l_min = 16 columns so that the spectrum it yields carries
+the 16 values the rank model reads at the next step.
 
 MLP: input 18 features (top-16 log10 singular values of the previous step at
 that bond, relative to the largest; bond index / L; min(step / 1000, 1)),
@@ -87,13 +90,17 @@ def mlp_loss_grad(P, X, y):
 
 
 # ---------------------------------------------------------------- randomized truncation
-def rsvd_truncate(C, k, omega, chi_max, delta, p=8, eta=0.05, floor_rel=1e-12, l_min=16):
+def rsvd_truncate(C, k, omega, chi_max, delta, p=8, eta=0.2, floor_rel=1e-12, l_min=16, q=1):
     """Randomized truncation of C at target rank k.  Returns
     (accepted, r, U*S (m x r), Vt (r x n), err_r^2, residual^2).  Residuals
     below (floor_rel ||C||)^2 count as round-off (a sample that spans C)."""
     m, n = C.shape
     l = min(max(k + p, l_min), m, n)
     Y = C @ omega[:n, :l]
+    for _ in range(q):
+        Qy, _ = qr_pos(Y)
+        Z, _ = qr_pos(C.T @ Qy)
+        Y = C @ Z
     Q, _ = qr_pos(Y)
     B = Q.T @ C
     U, S, Vt = np.linalg.svd(B, full_matrices=False)
@@ -113,13 +120,15 @@ def rsvd_truncate(C, k, omega, chi_max, delta, p=8, eta=0.05, floor_rel=1e-12, l
     full_cap = min(chi_max, m, n)
     rule_ok = (np.sqrt(err2) <= delta) or (r == full_cap) or (r == chi_max)
     floor2 = (floor_rel * np.sqrt(np.sum(C * C))) ** 2
-    accepted = bool(rule_ok and resid2 <= max(eta * max(err2, delta * delta), floor2))
+    accepted = bool(rule_ok and (np.sqrt(err2) <= delta or resid2 <= max(eta * err2, floor2)))
     return accepted, r, (Q @ U[:, :r]) * S[None, :r], Vt[:r], err2, resid2
 
 
-def round_mps_learned(cores, chi_max, eps, targets, omega, p=8, eta=0.05, spectra=None):
+def round_mps_learned(cores, chi_max, eps, targets, omega, p=8, eta=0.2, spectra=None, q=1):
     """round_mps with the randomized truncation at target ranks targets[k]
-    (bond k, 1 <= k < L; None = full SVD) and the full SVD as fallback.
+    (bond k, 1 <= k < L; None or 0 = full SVD) and the full SVD as fallback.
+    Bonds whose sample would cover the whole matrix (l = min(m, n)) take the
+    full SVD directly.
     Returns (cores, n_accepted, n_fallback).  If `spectra` is a dict, the full
     or randomized singular values of each bond are stored in it."""
     L = len(cores)
@@ -131,8 +140,9 @@ def round_mps_learned(cores, chi_max, eps, targets, omega, p=8, eta=0.05, spectr
         r0, d, r1 = A[k].shape
         Cm = A[k].reshape(r0, d * r1)
         done = False
-        if targets is not None and targets[k] is not None:
-            ok, r, US, Vt, _, _ = rsvd_truncate(Cm, int(targets[k]), omega, chi_max, delta, p, eta)
+        tk = None if targets is None or targets[k] is None else min(int(targets[k]), chi_max)
+        if tk and min(max(tk + p, 16), r0, d * r1) < min(r0, d * r1):
+            ok, r, US, Vt, _, _ = rsvd_truncate(Cm, tk, omega, chi_max, delta, p, eta, q=q)
             if ok:
                 n_acc += 1
                 done = True

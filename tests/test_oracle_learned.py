@@ -66,10 +66,43 @@ def test_round_learned_without_targets_is_round():
     a, na, nf = LR.round_mps_learned(A, 6, 1e-12, None, omega)
     b = M.round_mps(A, 6, 1e-12)
     np.testing.assert_allclose(M.to_tensor(a), M.to_tensor(b), atol=1e-12)
-    # generous targets: every bond accepted, same tensor
-    c, na, nf = LR.round_mps_learned(A, 64, 0.0, [None] + [16] * (L - 1), omega)
-    assert na == L - 1 and nf == 0
-    np.testing.assert_allclose(M.to_tensor(c), M.to_tensor(A), atol=1e-12)
+    assert na == 0 and nf == 0
+
+
+def test_round_learned_redundant_sum_is_exact():
+    """A + 0.5 A has twice the bond of its rank: the sample at target = rank
+    covers the range, every randomized step is accepted, result 1.5 A."""
+    L = 12
+    A = synth.random_mps(L, synth.feasible_ranks(L, 16), 4)
+    S = M.add(A, M.scale(A, 0.5))
+    omega = synth.gaussian_matrix(128, 128, 8)
+    c, na, nf = LR.round_mps_learned(S, 64, 1e-12, [0] + [16] * (L - 1) + [0], omega)
+    assert na >= 3 and nf == 0
+    np.testing.assert_allclose(M.to_tensor(c), 1.5 * M.to_tensor(A), atol=1e-11)
+
+
+def test_certificate_lower_bound_and_near_optimality():
+    """The inequality the certificate rests on: opt(r)^2 >= err(r)^2 - ||E||^2
+    (Ky Fan on C^T C = B^T B + E^T E), checked against the exact SVD; and every
+    accepted chi-capped truncation is within 1 / (1 - eta) of the optimum."""
+    omega = synth.gaussian_matrix(128, 128, 9)
+    rng = np.random.default_rng(10)
+    n_acc = 0
+    for trial in range(12):
+        m, n = 70 + trial, 64
+        s = np.exp(-rng.uniform(0.02, 0.3) * np.arange(n))
+        C = _mat(m, n, s, 100 + trial)
+        for k, q in ((20, 0), (20, 1), (32, 1)):
+            ok, r, US, Vt, err2, res2 = LR.rsvd_truncate(C, k, omega, k, 0.0, q=q)
+            sv = np.linalg.svd(C, compute_uv=False)
+            opt2 = np.sum(sv[r:] ** 2)
+            true2 = np.sum((C - US @ Vt) ** 2)
+            assert abs(true2 - err2) <= 1e-10 * np.sum(sv ** 2)
+            assert opt2 >= err2 - res2 - 1e-12 * np.sum(sv ** 2)
+            if ok:
+                n_acc += 1
+                assert err2 <= opt2 / (1 - 0.2) * (1 + 1e-10)
+    assert n_acc > 0
 
 
 def test_spectrum_features():
