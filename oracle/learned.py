@@ -124,11 +124,28 @@ def rsvd_truncate(C, k, omega, chi_max, delta, p=8, eta=0.2, floor_rel=1e-12, l_
     return accepted, r, (Q @ U[:, :r]) * S[None, :r], Vt[:r], err2, resid2
 
 
+def canonical_signs(US, Vt):
+    """Fix the sign freedom of each kept singular pair: the entry of largest
+    magnitude of every row of Vt (first one on ties) is made positive, and the
+    matching column of US flipped with it.  The randomized range finder draws
+    its sample in the frame of the right bond, so both implementations must
+    leave that frame in the same gauge for their samples to agree."""
+    US = US.copy()
+    Vt = Vt.copy()
+    for j in range(Vt.shape[0]):
+        i = int(np.argmax(np.abs(Vt[j])))
+        if Vt[j, i] < 0:
+            Vt[j] = -Vt[j]
+            US[:, j] = -US[:, j]
+    return US, Vt
+
+
 def round_mps_learned(cores, chi_max, eps, targets, omega, p=8, eta=0.2, spectra=None, q=1):
     """round_mps with the randomized truncation at target ranks targets[k]
     (bond k, 1 <= k < L; None or 0 = full SVD) and the full SVD as fallback.
     Bonds whose sample would cover the whole matrix (l = min(m, n)) take the
     full SVD directly.
+    Every step leaves its singular pairs in the sign gauge of canonical_signs.
     Returns (cores, n_accepted, n_fallback).  If `spectra` is a dict, the full
     or randomized singular values of each bond are stored in it."""
     L = len(cores)
@@ -155,6 +172,7 @@ def round_mps_learned(cores, chi_max, eps, targets, omega, p=8, eta=0.2, spectra
             Vt = Vt[:r]
             if spectra is not None:
                 spectra[k] = S.copy()
+        US, Vt = canonical_signs(US, Vt)
         A[k] = Vt.reshape(r, d, r1)
         A[k - 1] = np.tensordot(A[k - 1], US, axes=(2, 0))
     return A, n_acc, n_fb
