@@ -124,17 +124,28 @@ def rsvd_truncate(C, k, omega, chi_max, delta, p=8, eta=0.2, floor_rel=1e-12, l_
     return accepted, r, (Q @ U[:, :r]) * S[None, :r], Vt[:r], err2, resid2
 
 
+SIGN_PROBE_STEP = 0.6180339887498949      # golden-ratio step of the probe weights
+
+
+def sign_probe(n):
+    """Weights w_c = frac((c + 1) * 0.618...) + 0.25 of the sign gauge: a
+    generic positive vector, so that no structured singular vector (entries of
+    equal magnitude, mirror symmetries) is orthogonal to it."""
+    c = np.arange(1, n + 1, dtype=np.float64) * SIGN_PROBE_STEP
+    return c - np.floor(c) + 0.25
+
+
 def canonical_signs(US, Vt):
-    """Fix the sign freedom of each kept singular pair: the entry of largest
-    magnitude of every row of Vt (first one on ties) is made positive, and the
-    matching column of US flipped with it.  The randomized range finder draws
-    its sample in the frame of the right bond, so both implementations must
-    leave that frame in the same gauge for their samples to agree."""
+    """Fix the sign freedom of each kept singular pair: every row of Vt gets a
+    positive inner product with the probe weights, and the matching column of
+    US is flipped with it.  The randomized range finder draws its sample in
+    the frame of the right bond, so both implementations must leave that frame
+    in the same gauge for their samples to agree."""
     US = US.copy()
     Vt = Vt.copy()
+    w = sign_probe(Vt.shape[1])
     for j in range(Vt.shape[0]):
-        i = int(np.argmax(np.abs(Vt[j])))
-        if Vt[j, i] < 0:
+        if float(Vt[j] @ w) < 0:
             Vt[j] = -Vt[j]
             US[:, j] = -US[:, j]
     return US, Vt

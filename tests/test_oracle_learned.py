@@ -147,3 +147,19 @@ def test_learned_rounding_is_gauge_independent():
     b, nb, nfb = LR.round_mps_learned(B, 16, 1e-12, tg, omega)
     assert na > 0 and (na, nf) == (nb, nfb)
     np.testing.assert_allclose(M.to_tensor(a), M.to_tensor(b), atol=1e-11 * np.abs(M.to_tensor(a)).max())
+
+
+def test_sign_gauge_on_tied_entries():
+    """Rows with entries of equal magnitude (where a largest-entry rule is
+    ambiguous) get the sign that makes their probe product positive."""
+    r2 = 1 / np.sqrt(2)
+    Vt = np.array([[r2, -r2], [-r2, r2], [-r2, -r2]])
+    US = np.eye(3)[:, :3] * np.array([1.0, 2.0, 3.0])
+    w = LR.sign_probe(2)
+    assert w[0] != w[1] and (w > 0).all()
+    U2, V2 = LR.canonical_signs(US, Vt)
+    assert (V2 @ w > 0).all()
+    np.testing.assert_array_equal(V2[0], Vt[0])
+    np.testing.assert_array_equal(V2[1], -Vt[1])
+    np.testing.assert_array_equal(V2[2], -Vt[2])
+    np.testing.assert_array_equal(U2 @ V2, US @ Vt)
