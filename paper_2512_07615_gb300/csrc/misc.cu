@@ -4,6 +4,7 @@
 //  - contraction of an MPS to a dense [x][y][z] field (Eq. MPS), for outputs
 //  - moments and velocity of the contracted populations (Eq. macro, App. A)
 //  - TT-SVD of a dense field (Eq. svd-comp), used to compress geometry masks
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -264,22 +265,39 @@ __global__ void to_site_order_kernel(const T* dense, int n, double* out) {
   }
 }
 
-// G += M[:, chunk] M[:, chunk]^T over one column chunk per block (upper triangle)
-__global__ void gram_kernel(const double* M, int m, size_t ncols, int kc, double* G) {
+// Partial Gram matrices, deterministic: block p accumulates M[:, chunk] M[:, chunk]^T
+// (upper triangle) over the column chunks p, p + P, p + 2P, ... into its own
+// slice part[p] (every entry owned by one thread); gram_reduce_kernel sums the
+// slices in block order.
+__global__ void gram_part_kernel(const double* M, int m, size_t ncols, int kc, int P, double* part) {
   extern __shared__ double tile[];           // m x kc
-  const size_t c0 = (size_t)blockIdx.x * kc;
-  const int w = (int)((ncols - c0) < (size_t)kc ? (ncols - c0) : (size_t)kc);
-  for (int e = threadIdx.x; e < m * kc; e += blockDim.x) {
-    const int i = e / kc, c = e % kc;
-    tile[e] = c < w ? M[(size_t)i * ncols + c0 + c] : 0.0;
+  double* G = part + (size_t)blockIdx.x * m * m;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) G[e] = 0.0;
+  const size_t nch = (ncols + kc - 1) / kc;
+  for (size_t ch = blockIdx.x; ch < nch; ch += P) {
+    const size_t c0 = ch * kc;
+    const int w = (int)((ncols - c0) < (size_t)kc ? (ncols - c0) : (size_t)kc);
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * kc; e += blockDim.x) {
+      const int i = e / kc, c = e % kc;
+      tile[e] = c < w ? M[(size_t)i * ncols + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = e / m, j = e % m;
+      if (j < i) continue;
+      double acc = 0.0;
+      for (int c = 0; c < w; ++c) acc += tile[i * kc + c] * tile[j * kc + c];
+      G[e] += acc;
+    }
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    const int i = e / m, j = e % m;
-    if (j < i) continue;
-    double acc = 0.0;
-    for (int c = 0; c < w; ++c) acc += tile[i * kc + c] * tile[j * kc + c];
-    atomicAdd(&G[(size_t)i * m + j], acc);
+}
+
+__global__ void gram_reduce_kernel(const double* part, int P, size_t mm, double* G) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int p = 0; p < P; ++p) a += part[(size_t)p * mm + e];
+    G[e] = a;
   }
 }
 
@@ -363,12 +381,20 @@ __global__ void cast_store_kernel(const double* src, size_t n, T* dst) {
     dst[i] = (T)src[i];
 }
 
-__global__ void norm2_kernel(const double* x, size_t n, double* out) {
+// per-block partial sums of squares (summed in block order by the host)
+__global__ void norm2_part_kernel(const double* x, size_t n, double* part) {
+  __shared__ double red[32];
   double a = 0.0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     a += x[i] * x[i];
   for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
 }
 
 template <typename T>
@@ -379,9 +405,14 @@ int tt_svd_dense(const T* d_dense, int n, T* d_dst, int* d_dst_ranks, int dst_ca
   const int mmax = 2 * imin(chi_max, dst_cap);
   if (mmax > 1024) return TNLBM_E_ARG;
   double *M = nullptr, *M2 = nullptr, *G = nullptr, *Wm = nullptr, *Vm = nullptr, *U = nullptr, *nrm = nullptr;
+  double* gpart = nullptr;
   int* d_r = nullptr;
+  // partial Gram slices: as many as fit in 256 MB at the largest m (at most 304)
+  const int NB_NORM = 152 * 4;
+  int Pg = (int)std::min<size_t>(304, std::max<size_t>(1, ((size_t)256 << 20) / ((size_t)mmax * mmax * sizeof(double))));
   auto cleanup = [&]() {
     cudaFree(M); cudaFree(M2); cudaFree(G); cudaFree(Wm); cudaFree(Vm); cudaFree(U); cudaFree(nrm); cudaFree(d_r);
+    cudaFree(gpart);
   };
   if (cudaMalloc(&M, total * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&M2, total * sizeof(double)) != cudaSuccess ||
@@ -389,27 +420,30 @@ int tt_svd_dense(const T* d_dense, int n, T* d_dst, int* d_dst_ranks, int dst_ca
       cudaMalloc(&Wm, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&Vm, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&U, (size_t)mmax * mmax * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&nrm, sizeof(double)) != cudaSuccess || cudaMalloc(&d_r, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&nrm, NB_NORM * sizeof(double)) != cudaSuccess || cudaMalloc(&d_r, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&gpart, (size_t)Pg * mmax * mmax * sizeof(double)) != cudaSuccess) {
     cleanup();
     return TNLBM_E_OOM;
   }
   to_site_order_kernel<T><<<152 * 8, 256, 0, st>>>(d_dense, n, M);
-  cudaMemsetAsync(nrm, 0, sizeof(double), st);
-  norm2_kernel<<<152 * 4, 256, 0, st>>>(M, total, nrm);
-  double h_n2 = 0.0;
-  cudaMemcpyAsync(&h_n2, nrm, sizeof(double), cudaMemcpyDeviceToHost, st);
+  norm2_part_kernel<<<NB_NORM, 256, 0, st>>>(M, total, nrm);
+  std::vector<double> h_part(NB_NORM);
+  cudaMemcpyAsync(h_part.data(), nrm, NB_NORM * sizeof(double), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
+  double h_n2 = 0.0;
+  for (double v : h_part) h_n2 += v;
   const double delta = eps * sqrt(h_n2) / sqrt((double)(L - 1));
   std::vector<int> ranks(L + 1, 1);
   int r = 1;
   for (int k = 0; k < L - 1; ++k) {
     const int m = 2 * r;
     const size_t ncols = total >> (k + 1);
-    cudaMemsetAsync(G, 0, (size_t)m * m * sizeof(double), st);
     int kc = 6144 / m;
     if (kc < 1) kc = 1;
-    const size_t nblk = (ncols + kc - 1) / kc;
-    gram_kernel<<<(unsigned)nblk, 256, (size_t)m * kc * sizeof(double), st>>>(M, m, ncols, kc, G);
+    const size_t nch = (ncols + kc - 1) / kc;
+    const int P = (int)std::min<size_t>((size_t)Pg, nch);
+    gram_part_kernel<<<P, 256, (size_t)m * kc * sizeof(double), st>>>(M, m, ncols, kc, P, gpart);
+    gram_reduce_kernel<<<152, 256, 0, st>>>(gpart, P, (size_t)m * m, G);
     gram_eig_kernel<<<1, 1024, 0, st>>>(G, m, Wm, Vm, U, imin(chi_max, dst_cap), delta * delta,
                                         (int)(ncols < (size_t)1024 ? ncols : (size_t)1024), d_r, d_status);
     int h_r = 0;
