@@ -235,6 +235,86 @@ int tnlbm_from_dense(int precision, int n_bits, const void *dense, void *dst,
                      int *dst_ranks, int dst_cap, int chi_max, double eps,
                      void *stream);
 
+/* ------------------------------------------------------------------ learned rounding
+ * Not part of the paper: the full SVD of each right-to-left step of the
+ * rounding (Eq. svd-move) may be replaced by a randomized truncation at a
+ * target rank k, which is accepted only when its error is certified.
+ *   l = min(max(k + oversample, 16), m, n) samples;  Y = C Omega[:n, :l];
+ *   `power` times: Y = C orth(C^T orth(Y))  (orth = Householder Q factor);
+ *   Q = orth(Y);  B = Q^T C;  B = U S V^T (one-sided Jacobi);
+ *   err(r)^2 = ||C - Q B||_F^2 + sum_{j>=r} s_j^2  (exact, measured);
+ *   r = smallest rank <= chi_max with err(r) <= delta (delta as in the full
+ *   rounding), accepted iff that rule is met inside the sample (or r reaches
+ *   chi_max) and either err(r) <= delta or ||C - Q B||^2 <= max(eta err(r)^2,
+ *   (floor_rel ||C||_F)^2) -- the latter proves err(r)^2 <= opt(r)^2/(1-eta)
+ *   (Ky Fan on C^T C = B^T B + E^T E); otherwise the full SVD runs on C.
+ * C is the m x n centre matrix of the step.  Omega is a fixed Gaussian matrix
+ * supplied by the caller (row-major, omega_rows x omega_ld); the randomized
+ * path is skipped where n > omega_rows or l > omega_ld. */
+
+/* tnlbm_lincomb_round with the randomized truncation at given target ranks.
+ * targets: host, batch x (3 n_bits + 1) ints, entry k = target at bond k
+ * (0 = full SVD there; entries 0 and L are ignored).  omega: DEVICE array of
+ * the precision's type.  counters (host int[3], may be NULL) receives
+ * accepted / fell back / full-SVD step counts.  0 < eta < 1, floor_rel >= 0,
+ * 0 <= power <= 4.
+ * Synchronous on `stream`. */
+int tnlbm_lincomb_round_rsvd(int precision, int n_bits, int batch, int nterms,
+                             const tnlbm_term *terms, void *const *dst,
+                             int *const *dst_ranks, int dst_cap, int chi_max,
+                             double eps, const int *targets, const void *omega,
+                             int omega_rows, int omega_ld, int oversample,
+                             int power, double eta, double floor_rel,
+                             int *counters, void *stream);
+
+/* Rank model: 18 -> 64 -> 64 -> 1 ReLU network mapping a bond's features
+ * (top-16 log10 singular values of the previous step relative to the largest,
+ * padded with -20; bond / L; min(step / 1000, 1)) to retained rank / chi_max.
+ * Parameters: one flat array of tnlbm_mlp_param_count() values, W1[64][18],
+ * b1[64], W2[64][64], b2[64], W3[64], b3.  Forward and backward passes use the
+ * parameters rounded to FP16, with FP32 arithmetic.  All pointers are DEVICE
+ * pointers; X is M x 18 row-major FP32, y and out are M FP32 values.
+ * Asynchronous on `stream`. */
+int tnlbm_mlp_param_count(void);
+int tnlbm_mlp_forward(const float *params, int M, const float *X, float *out,
+                      void *stream);
+/* loss = mean (out - y)^2 (device float), grad = d loss / d params (device). */
+int tnlbm_mlp_loss_grad(const float *params, int M, const float *X,
+                        const float *y, float *loss, float *grad, void *stream);
+/* `iters` Adam steps (beta 0.9 / 0.999, eps 1e-8, rate lr) on minibatches of
+ * `batch` consecutive samples (cyclic over the M samples; shuffle beforehand),
+ * starting at Adam step step0 (0 for a fresh start).  master (FP32), adam_m and
+ * adam_v (zero for a fresh start) are updated in place; half_out (device
+ * __half[param_count], may be NULL) receives the FP16 copy after every step;
+ * loss_hist (device float[iters], may be NULL) the minibatch losses. */
+int tnlbm_mlp_train(float *master, float *adam_m, float *adam_v, void *half_out,
+                    int M, const float *X, const float *y, int iters, int batch,
+                    int step0, float lr, float *loss_hist, void *stream);
+
+/* Learned rounding inside a simulation.  mode 0: off (the default; the step is
+ * unchanged).  mode 1: every rounding step logs its spectrum; from the second
+ * step on, each step also appends one training row per bond (the 18 features
+ * of the previous step's spectrum at that bond, then the rank kept now /
+ * chi_max) to a device log of dataset_cap rows.  mode 2: as mode 1, and the
+ * rank model (tnlbm_learn_set_mlp, required first) predicts each bond's target
+ * rank from the previous step's spectrum for the randomized truncation above.
+ * mode 3: as mode 2 with the previous step's kept rank as the target (the
+ * baseline the rank model is measured against).
+ * omega: HOST doubles, omega_rows >= 2 chi_max.  Re-captures the step graph;
+ * clears the logs and counters. */
+int tnlbm_learn_configure(tnlbm_sim *s, int mode, const double *omega,
+                          int omega_rows, int omega_ld, int oversample,
+                          int power, double eta, double floor_rel,
+                          int dataset_cap);
+/* Copies the FP16 rank model (host or device pointer, param_count values). */
+int tnlbm_learn_set_mlp(tnlbm_sim *s, const void *params_f16);
+/* Copies up to cap logged rows (19 floats each) to out (host or device);
+ * *count = rows logged so far (may exceed the log's capacity). */
+int tnlbm_learn_dataset(tnlbm_sim *s, float *out, int cap, int *count,
+                        int reset);
+/* out[0..2]: randomized truncations accepted, fallen back, full SVDs. */
+int tnlbm_learn_counters(tnlbm_sim *s, long long *out, int reset);
+
 #ifdef __cplusplus
 }
 #endif

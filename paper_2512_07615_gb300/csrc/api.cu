@@ -152,6 +152,20 @@ struct tnlbm_sim {
   int launches_per_step = 0;
   int64_t steps = 0;
   int pending_status = 0;
+  // learned rounding (rank model + randomized truncation); off until configured
+  int learn_mode = 0;            // 0 off, 1 log spectra, 2 predict ranks
+  LearnCtx h_learn{};
+  LearnCtx* d_learn = nullptr;
+  JobLog* d_logs = nullptr;
+  int n_logs = 0;
+  int* d_step = nullptr;
+  int* d_lcount = nullptr;       // [0] accepted, [1] fell back, [2] full SVDs, [3] dataset rows
+  void* d_omega = nullptr;
+  size_t omega_bytes = 0;
+  float* d_dataset = nullptr;
+  int dataset_cap = 0;
+  __half* d_mlp = nullptr;
+  bool mlp_set = false;
 };
 
 namespace tn {
@@ -475,7 +489,7 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
       n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof);
     if (!lv.rj.empty()) {
       launch_round<T>(lv.d_rj, (int)lv.rj.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal,
-                      s->d_status, s->s0, ctr);
+                      s->d_status, s->s0, ctr, s->learn_mode ? s->d_learn : nullptr);
       if (prof) prof->mark(C_ROUND);
       ++n;
     }
@@ -492,8 +506,97 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
   launch_copy<T>(s->d_copy_src, s->d_copy_dst, s->lat.Q, s->L, s->s0);
   if (prof) prof->mark(C_COPY);
   ++n;
+  if (s->learn_mode) {
+    launch_learn_tick(s->d_step, s->s0);
+    ++n;
+  }
   *launches = n;
   return 0;
+}
+
+// (re)capture one step as a graph
+template <typename T>
+static int capture_graph(tnlbm_sim* s) {
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  if (s->gexec) { cudaGraphExecDestroy(s->gexec); s->gexec = nullptr; }
+  if (s->graph) { cudaGraphDestroy(s->graph); s->graph = nullptr; }
+  TN_CUDA(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  enqueue_step<T>(s, &launches);
+  TN_CUDA(cudaStreamEndCapture(s->s0, &s->graph));
+  TN_CUDA(cudaGraphInstantiate(&s->gexec, s->graph, 0));
+  s->launches_per_step = launches;
+  return 0;
+}
+
+// Switch the learned rounding of a simulation (see tnlbm_learn_configure).
+template <typename T>
+static int learn_configure_impl(tnlbm_sim* s, int mode, const double* omega, int rows, int ld,
+                                int oversample, int power, double eta, double floor_rel, int dataset_cap) {
+  if (!s->d_learn) {
+    int nj = 0;
+    for (auto& lv : s->levels) nj += (int)lv.rj.size();
+    s->n_logs = nj;
+    s->d_learn = (LearnCtx*)s->arena.alloc(sizeof(LearnCtx));
+    s->d_logs = (JobLog*)s->arena.alloc(std::max(nj, 1) * sizeof(JobLog));
+    s->d_step = (int*)s->arena.alloc(sizeof(int));
+    s->d_lcount = (int*)s->arena.alloc(4 * sizeof(int));
+    s->d_mlp = (__half*)s->arena.alloc(MLP_NPARAM * sizeof(__half));
+    if (!s->d_learn || !s->d_logs || !s->d_step || !s->d_lcount || !s->d_mlp) {
+      set_error("out of device memory for the learned rounding");
+      return TNLBM_E_OOM;
+    }
+    TN_CUDA(cudaMemset(s->d_mlp, 0, MLP_NPARAM * sizeof(__half)));
+  }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  if (mode > 0) {
+    const size_t ob = (size_t)rows * ld * sizeof(T);
+    if (ob > s->omega_bytes) {
+      s->d_omega = s->arena.alloc(ob);
+      if (!s->d_omega) { set_error("out of device memory for omega"); return TNLBM_E_OOM; }
+      s->omega_bytes = ob;
+    }
+    std::vector<T> ho((size_t)rows * ld);
+    for (size_t i = 0; i < ho.size(); ++i) ho[i] = (T)omega[i];
+    TN_CUDA(cudaMemcpy(s->d_omega, ho.data(), ob, cudaMemcpyHostToDevice));
+    if (dataset_cap > s->dataset_cap) {
+      s->d_dataset = (float*)s->arena.alloc((size_t)dataset_cap * (MLP_IN + 1) * sizeof(float));
+      if (!s->d_dataset) { set_error("out of device memory for the spectrum log"); return TNLBM_E_OOM; }
+      s->dataset_cap = dataset_cap;
+    }
+  }
+  const int step = (int)std::min<int64_t>(s->steps, 1 << 30);
+  TN_CUDA(cudaMemcpy(s->d_step, &step, sizeof(int), cudaMemcpyHostToDevice));
+  TN_CUDA(cudaMemset(s->d_lcount, 0, 4 * sizeof(int)));
+  TN_CUDA(cudaMemset(s->d_logs, 0, std::max(s->n_logs, 1) * sizeof(JobLog)));
+  LearnCtx& h = s->h_learn;
+  h = LearnCtx{};
+  h.omega = s->d_omega;
+  h.omega_rows = rows;
+  h.omega_ld = ld;
+  h.oversample = oversample;
+  h.power = power;
+  h.eta = (float)eta;
+  h.floor_rel = (float)floor_rel;
+  h.mlp = s->d_mlp;
+  h.step = s->d_step;
+  h.dataset = dataset_cap > 0 ? s->d_dataset : nullptr;
+  h.dataset_count = s->d_lcount + 3;
+  h.dataset_cap = dataset_cap;
+  h.counters = s->d_lcount;
+  TN_CUDA(cudaMemcpy(s->d_learn, &h, sizeof(LearnCtx), cudaMemcpyHostToDevice));
+  int idx = 0;
+  for (auto& lv : s->levels) {
+    for (auto& rj : lv.rj) {
+      rj.rsvd_mode = (mode >= 2) ? mode : 0;
+      rj.log = mode > 0 ? s->d_logs + idx : nullptr;
+      ++idx;
+    }
+    if (!lv.rj.empty())
+      TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
+  }
+  s->learn_mode = mode;
+  return capture_graph<T>(s);
 }
 
 // one-off rounding jobs (initial states): terms over nodes
@@ -700,14 +803,8 @@ static int create_impl(tnlbm_sim* s) {
     for (double v : hm) m0 += v;
     cudaMemcpy(s->d_mass0, &m0, sizeof(double), cudaMemcpyHostToDevice);
   }
-  // capture one step as a graph
-  TN_CUDA(cudaStreamSynchronize(s->s0));
-  TN_CUDA(cudaStreamBeginCapture(s->s0, cudaStreamCaptureModeThreadLocal));
-  int launches = 0;
-  enqueue_step<T>(s, &launches);
-  TN_CUDA(cudaStreamEndCapture(s->s0, &s->graph));
-  TN_CUDA(cudaGraphInstantiate(&s->gexec, s->graph, 0));
-  s->launches_per_step = launches;
+  rc = capture_graph<T>(s);
+  if (rc) return rc;
   int st[STATUS_INTS] = {0};
   TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st[0]) return status_to_code(st);
@@ -889,6 +986,68 @@ int tnlbm_stats_get(tnlbm_sim* s, tnlbm_stats* out) {
   return 0;
 }
 
+int tnlbm_learn_configure(tnlbm_sim* s, int mode, const double* omega, int omega_rows, int omega_ld,
+                          int oversample, int power, double eta, double floor_rel, int dataset_cap) {
+  if (!s || mode < 0 || mode > 3 ||
+      (mode > 0 && (!omega || omega_rows < 2 * s->cfg.chi_max || omega_ld < 1 || oversample < 0 ||
+                    power < 0 || power > 4 || !(eta > 0.0) || !(eta < 1.0) || floor_rel < 0.0 ||
+                    dataset_cap < 0))) {
+    set_error("bad arguments to tnlbm_learn_configure");
+    return TNLBM_E_ARG;
+  }
+  if (mode == 2 && !s->mlp_set) {
+    set_error("tnlbm_learn_configure: mode 2 needs a rank model (tnlbm_learn_set_mlp)");
+    return TNLBM_E_ARG;
+  }
+  return s->prec == TNLBM_FP64
+             ? tn::learn_configure_impl<double>(s, mode, omega, omega_rows, omega_ld, oversample, power, eta, floor_rel, dataset_cap)
+             : tn::learn_configure_impl<float>(s, mode, omega, omega_rows, omega_ld, oversample, power, eta, floor_rel, dataset_cap);
+}
+
+int tnlbm_learn_set_mlp(tnlbm_sim* s, const void* params_f16) {
+  if (!s || !params_f16) { set_error("bad arguments to tnlbm_learn_set_mlp"); return TNLBM_E_ARG; }
+  if (!s->d_learn) {
+    // allocate the learning state (mode stays off)
+    std::vector<double> om(2 * (size_t)s->cfg.chi_max, 0.0);
+    int rc = s->prec == TNLBM_FP64
+                 ? tn::learn_configure_impl<double>(s, 0, om.data(), 2 * s->cfg.chi_max, 1, 0, 0, 0.5, 0.0, 0)
+                 : tn::learn_configure_impl<float>(s, 0, om.data(), 2 * s->cfg.chi_max, 1, 0, 0, 0.5, 0.0, 0);
+    if (rc) return rc;
+  }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  TN_CUDA(cudaMemcpy(s->d_mlp, params_f16, tn::MLP_NPARAM * sizeof(__half), cudaMemcpyDefault));
+  s->mlp_set = true;
+  return 0;
+}
+
+int tnlbm_learn_dataset(tnlbm_sim* s, float* out, int cap, int* count, int reset) {
+  if (!s || cap < 0 || (cap > 0 && !out) || !count) { set_error("bad arguments to tnlbm_learn_dataset"); return TNLBM_E_ARG; }
+  *count = 0;
+  if (!s->d_learn) return 0;
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  int hc[4] = {0};
+  TN_CUDA(cudaMemcpy(hc, s->d_lcount, sizeof(hc), cudaMemcpyDeviceToHost));
+  const int stored = std::min(hc[3], s->h_learn.dataset_cap);
+  const int n = std::min(stored, cap);
+  if (n > 0)
+    TN_CUDA(cudaMemcpy(out, s->d_dataset, (size_t)n * (tn::MLP_IN + 1) * sizeof(float), cudaMemcpyDefault));
+  *count = hc[3];
+  if (reset) TN_CUDA(cudaMemset(s->d_lcount + 3, 0, sizeof(int)));
+  return 0;
+}
+
+int tnlbm_learn_counters(tnlbm_sim* s, long long* out, int reset) {
+  if (!s || !out) { set_error("bad arguments to tnlbm_learn_counters"); return TNLBM_E_ARG; }
+  out[0] = out[1] = out[2] = 0;
+  if (!s->d_learn) return 0;
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  int hc[4] = {0};
+  TN_CUDA(cudaMemcpy(hc, s->d_lcount, sizeof(hc), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 3; ++i) out[i] = hc[i];
+  if (reset) TN_CUDA(cudaMemset(s->d_lcount, 0, 3 * sizeof(int)));
+  return 0;
+}
+
 int tnlbm_destroy(tnlbm_sim* s) {
   if (!s) return 0;
   if (s->s0) cudaStreamSynchronize(s->s0);
@@ -922,10 +1081,18 @@ static int check_status(int* d_status, cudaStream_t st) {
   return status_to_code(h);
 }
 
+struct RsvdArgs {               // randomized truncation at given target ranks
+  const int* targets;           // host, batch x (L + 1); 0 = full SVD at that bond
+  const void* omega;            // device, element type of the rounding, rows x ld
+  int rows, ld, oversample, power;
+  double eta, floor_rel;
+  int* counters;                // host [3]: accepted, fell back, full SVDs
+};
+
 template <typename T>
 static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* terms, void* const* dst,
                         int* const* dst_ranks, int dst_cap, int chi, double eps, int materialize,
-                        cudaStream_t st) {
+                        cudaStream_t st, const RsvdArgs* ra = nullptr) {
   const int L = 3 * n_bits;
   std::vector<RoundJob> jobs(batch);
   std::vector<T> masks;
@@ -975,22 +1142,49 @@ static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* ter
   }
   size_t tot = 0;
   for (auto& j : jobs) tot += j.lay.total;
-  DevBuf scr, dj, dm, ds, dsc;
+  DevBuf scr, dj, dm, ds, dsc, dtg, dlc, dcnt;
   if (!scr.alloc(tot * sizeof(T)) || !dj.alloc(batch * sizeof(RoundJob)) ||
       !dm.alloc(std::max<size_t>(masks.size(), 2) * sizeof(T)) || !ds.alloc(STATUS_INTS * sizeof(int)) ||
-      !dsc.alloc(SC_COUNT * sizeof(double))) {
+      !dsc.alloc(SC_COUNT * sizeof(double)) ||
+      (ra && (!dtg.alloc((size_t)batch * (L + 1) * sizeof(int)) || !dlc.alloc(sizeof(LearnCtx)) ||
+              !dcnt.alloc(4 * sizeof(int))))) {
     set_error("out of device memory");
     return TNLBM_E_OOM;
   }
   size_t o = 0;
   for (auto& j : jobs) { j.scratch = (T*)scr.p + o; o += j.lay.total; }
+  if (ra) {
+    for (int b = 0; b < batch; ++b) {
+      jobs[b].rsvd_mode = 1;
+      jobs[b].targets = (const int*)dtg.p + (size_t)b * (L + 1);
+    }
+    LearnCtx h{};
+    h.omega = ra->omega;
+    h.omega_rows = ra->rows;
+    h.omega_ld = ra->ld;
+    h.oversample = ra->oversample;
+    h.power = ra->power;
+    h.eta = (float)ra->eta;
+    h.floor_rel = (float)ra->floor_rel;
+    h.counters = (int*)dcnt.p;
+    TN_CUDA(cudaMemcpyAsync(dtg.p, ra->targets, (size_t)batch * (L + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    TN_CUDA(cudaMemcpyAsync(dlc.p, &h, sizeof(LearnCtx), cudaMemcpyHostToDevice, st));
+    TN_CUDA(cudaMemsetAsync(dcnt.p, 0, 4 * sizeof(int), st));
+  }
   TN_CUDA(cudaMemcpyAsync(dj.p, jobs.data(), batch * sizeof(RoundJob), cudaMemcpyHostToDevice, st));
   if (!masks.empty()) TN_CUDA(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
   TN_CUDA(cudaMemsetAsync(dsc.p, 0, SC_COUNT * sizeof(double), st));
-  launch_round<T>((const RoundJob*)dj.p, batch, L, n_bits, (const T*)dm.p, (const double*)dsc.p, (int*)ds.p, st);
+  launch_round<T>((const RoundJob*)dj.p, batch, L, n_bits, (const T*)dm.p, (const double*)dsc.p, (int*)ds.p, st,
+                  nullptr, ra ? (const LearnCtx*)dlc.p : nullptr);
   TN_CUDA(cudaGetLastError());
-  return check_status((int*)ds.p, st);
+  int rc = check_status((int*)ds.p, st);
+  if (ra && ra->counters) {
+    int hc[4] = {0};
+    TN_CUDA(cudaMemcpy(hc, dcnt.p, sizeof(hc), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 3; ++i) ra->counters[i] = hc[i];
+  }
+  return rc;
 }
 
 template <typename T>
@@ -1053,6 +1247,30 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const 
   return precision == TNLBM_FP64
              ? tn::lincomb_impl<double>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st)
              : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st);
+}
+
+int tnlbm_lincomb_round_rsvd(int precision, int n_bits, int batch, int nterms, const tnlbm_term* terms,
+                             void* const* dst, int* const* dst_ranks, int dst_cap, int chi_max, double eps,
+                             const int* targets, const void* omega, int omega_rows, int omega_ld,
+                             int oversample, int power, double eta, double floor_rel, int* counters,
+                             void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || nterms < 1 || nterms > TN_MAXT || !terms || !dst ||
+      !dst_ranks || chi_max < 1 || chi_max > dst_cap || chi_max > 512 || eps < 0 || !targets || !omega ||
+      omega_rows < 1 || omega_ld < 1 || oversample < 0 || power < 0 || power > 4 || !(eta > 0.0) ||
+      !(eta < 1.0) || floor_rel < 0.0 ||
+      (precision != TNLBM_FP64 && precision != TNLBM_FP32)) {
+    set_error("bad arguments to tnlbm_lincomb_round_rsvd");
+    return TNLBM_E_ARG;
+  }
+  if (counters) counters[0] = counters[1] = counters[2] = 0;
+  if (batch == 0) return 0;
+  for (int i = 0; i < batch * (3 * n_bits + 1); ++i)
+    if (targets[i] < 0) { set_error("negative target rank"); return TNLBM_E_ARG; }
+  cudaStream_t st = (cudaStream_t)stream;
+  tn::RsvdArgs ra{targets, omega, omega_rows, omega_ld, oversample, power, eta, floor_rel, counters};
+  return precision == TNLBM_FP64
+             ? tn::lincomb_impl<double>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st, &ra)
+             : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st, &ra);
 }
 
 int tnlbm_materialize(int precision, int n_bits, int batch, const tnlbm_term* terms, void* const* dst,

@@ -2,6 +2,7 @@
 // descriptors, status codes and small device helpers.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
@@ -84,7 +85,32 @@ struct Term {
 // Scratch partition of one rounding job (elements of T), same on host and device.
 struct RoundLayout {
   size_t q_off[TN_MAXL + 1];  // left-orthogonal cores of the QR sweep
-  size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, total;
+  size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, rz_off, total;
+};
+
+// Learned-rank rounding state shared by all jobs of a launch (nullable parts).
+// Spectrum log of one job: top-16 log10(s_i / s_0) per bond and the rank kept.
+#define TN_SPEC 16
+struct JobLog {
+  float spec[TN_MAXL + 1][TN_SPEC];
+  int label[TN_MAXL + 1];
+  int valid[TN_MAXL + 1];
+};
+static constexpr int MLP_IN = 18, MLP_H = 64;
+static constexpr int MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+struct LearnCtx {
+  const void* omega;          // T*, fixed Gaussian test matrix (rows x ld)
+  int omega_rows, omega_ld;
+  int oversample;             // p
+  int power;                  // power steps of the range finder
+  float eta;                  // certificate: residual <= eta * err^2 at the chi cap
+  float floor_rel;            // residuals below (floor_rel ||C||)^2 are round-off
+  const __half* mlp;          // FP16 parameters (MLP_NPARAM), or null
+  const int* step;            // device step counter (MLP feature)
+  float* dataset;             // (features[18], label) rows, or null = no logging
+  int* dataset_count;
+  int dataset_cap;
+  int* counters;              // [0] randomized accepted, [1] fell back, [2] full SVDs
 };
 
 struct RoundJob {
@@ -98,6 +124,13 @@ struct RoundJob {
   int qb[TN_MAXL + 1];        // upper bounds of the QR-sweep bonds
   RoundLayout lay;
   int materialize_only;       // 1: write the (single) term to dst, no rounding
+  int rsvd_mode;              // 0 full SVD; 1 randomized at rsvd_k / targets; 2 MLP-predicted;
+                              // 3 previous step's rank
+  int rsvd_k;                 // fixed target rank (mode 1, when targets is null)
+  const int* targets;         // per-bond target ranks (mode 1), device, or null
+  JobLog* log;                // spectra of the previous step (modes 2 and logging), or null
+  const void* masks;          // T*, rank-1 mask table of this job's simulation, or null = launch's
+  const double* scal;         // scalars of this job's simulation, or null = launch's
 };
 
 // bound of one term's bond k from the capacities of its operands
@@ -134,7 +167,9 @@ int cuda_fail(cudaError_t e, const char* what);
 template <typename T>
 void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits,
                   const T* d_masks, const double* d_scal, int* d_status,
-                  cudaStream_t st, double* d_ctr = nullptr);
+                  cudaStream_t st, double* d_ctr = nullptr, const LearnCtx* d_learn = nullptr);
 size_t round_smem_bytes();
+// increments the device step counter read by the rank model
+void launch_learn_tick(int* d_step, cudaStream_t st);
 
 }  // namespace tn

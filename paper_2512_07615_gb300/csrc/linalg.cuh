@@ -449,3 +449,85 @@ __device__ int jacobi_cols_hw(T* Wm, int ldw, T* V, int ldv, int ncol, int len, 
 }
 
 }  // namespace tn
+
+namespace tn {
+
+// C (M x N, ldc) = A^T B with A given as K x M (lda) and B as K x N (ldb).
+template <typename T>
+__device__ void cta_gemm_tn(int M, int N, int K, const T* A, int lda, const T* B, int ldb, T* C, int ldc) {
+  const int tm = (M + 3) >> 2, tnn = (N + 3) >> 2;
+  for (int t = threadIdx.x; t < tm * tnn; t += blockDim.x) {
+    const int i0 = (t / tnn) * 4, j0 = (t % tnn) * 4;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int k = 0; k < K; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = (i0 + a < M) ? A[(size_t)k * lda + i0 + a] : (T)0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = (j0 + b < N) ? B[(size_t)k * ldb + j0 + b] : (T)0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (i0 + a >= M) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (j0 + b < N) C[(size_t)(i0 + a) * ldc + j0 + b] = acc[a][b];
+    }
+  }
+  __syncthreads();
+}
+
+// Rank-predicting MLP (18 -> 64 -> 64 -> 1, ReLU, FP16 parameters) evaluated
+// by the block; returns the predicted rank clamped to [1, chi].  `buf` is
+// shared scratch of >= 146 floats.  Parameter layout: W1[64][18], b1[64],
+// W2[64][64], b2[64], W3[64], b3.
+__device__ inline int mlp_predict_rank(const __half* P, const float* spec, float bondf, float stepf,
+                                       int chi, float* buf) {
+  float* x = buf;
+  float* h1 = buf + 18;
+  float* h2 = buf + 18 + 64;
+  if (threadIdx.x < 16) x[threadIdx.x] = spec[threadIdx.x];
+  if (threadIdx.x == 16) x[16] = bondf;
+  if (threadIdx.x == 17) x[17] = stepf;
+  __syncthreads();
+  const __half* W1 = P;
+  const __half* b1 = W1 + 64 * 18;
+  const __half* W2 = b1 + 64;
+  const __half* b2 = W2 + 64 * 64;
+  const __half* W3 = b2 + 64;
+  const __half* b3 = W3 + 64;
+  if (threadIdx.x < 64) {
+    float a = __half2float(b1[threadIdx.x]);
+    for (int i = 0; i < 18; ++i) a += __half2float(W1[threadIdx.x * 18 + i]) * x[i];
+    h1[threadIdx.x] = a > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    float a = __half2float(b2[threadIdx.x]);
+    for (int i = 0; i < 64; ++i) a += __half2float(W2[threadIdx.x * 64 + i]) * h1[i];
+    h2[threadIdx.x] = a > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  __shared__ int s_pred;
+  if (threadIdx.x < 32) {
+    float a = __half2float(W3[threadIdx.x]) * h2[threadIdx.x] + __half2float(W3[threadIdx.x + 32]) * h2[threadIdx.x + 32];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (threadIdx.x == 0) {
+      const float y = a + __half2float(b3[0]);
+      int k = isfinite(y) ? (int)lrintf(fminf(fmaxf(y, 0.f), 2.f) * (float)chi) : chi;
+      s_pred = k < 1 ? 1 : (k > chi ? chi : k);
+    }
+  }
+  __syncthreads();
+  return s_pred;
+}
+
+}  // namespace tn

@@ -33,7 +33,7 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   size_t off = 0;
   auto al = [&](size_t n) { size_t o = off; off += (n + 31) & ~(size_t)31; return o; };
   for (int k = 0; k < L; ++k) j.lay.q_off[k] = al((size_t)2 * j.qb[k] * (k == L - 1 ? 1 : j.qb[k + 1]));
-  size_t wmax = 0, mmax = 0, rmax = 0, cmax = 0, jw = 0, jv = 0, us = 0;
+  size_t wmax = 0, mmax = 0, rmax = 0, cmax = 0, jw = 0, jv = 0, us = 0, rz = 0;
   for (int k = 0; k < L; ++k) {
     size_t w = 0;
     for (int t = 0; t < j.nterms; ++t)
@@ -51,6 +51,7 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
     size_t len = j.qb[k] > (int)(2 * rn) ? j.qb[k] : 2 * rn;
     jw = ncol * len > jw ? ncol * len : jw;
     jv = ncol * ncol > jv ? ncol * ncol : jv;
+    rz = 2 * rn * ncol > rz ? 2 * rn * ncol : rz;     // range-finder power step: n x l
     size_t u = (size_t)j.qb[k] * imin(j.chi, (int)ncol);
     us = u > us ? u : us;
     // C' = Q_{k-1} (2 q_{k-1} x q_k) * US: 2 q_{k-1} x r
@@ -64,6 +65,7 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   j.lay.jw_off = al(jw);
   j.lay.jv_off = al(jv);
   j.lay.us_off = al(us);
+  j.lay.rz_off = al(rz);
   j.lay.total = off;
   (void)eb;
 }
@@ -184,11 +186,15 @@ struct PhaseClock {
 
 template <typename T>
 __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L,
-                                                   int n_bits, const T* __restrict__ masks,
-                                                   const double* __restrict__ scal,
+                                                   int n_bits, const T* __restrict__ masks_arg,
+                                                   const double* __restrict__ scal_arg,
                                                    int* __restrict__ status,
-                                                   double* __restrict__ ctr) {
+                                                   double* __restrict__ ctr,
+                                                   const LearnCtx* __restrict__ lc) {
   const RoundJob& J = jobs[blockIdx.x];
+  // per-job mask table and scalars (jobs of several simulations in one launch)
+  const T* __restrict__ masks = J.masks ? (const T*)J.masks : masks_arg;
+  const double* __restrict__ scal = J.scal ? J.scal : scal_arg;
   extern __shared__ __align__(16) unsigned char smem[];
   int* s_rt = (int*)smem;                            // [TN_MAXT][TN_MAXL+1] term bonds
   int* s_ro = s_rt + TN_MAXT * (TN_MAXL + 1);        // row offsets at each bond
@@ -349,109 +355,300 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
   int rnext = 1;
   for (int k = L - 1; k >= 1; --k) {
     const int m = s_q[k], n = 2 * rnext;
-    const int ncol = imin(m, n), len = imax(m, n);
-    if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
-    const bool trans = (n <= m);             // Jacobi on the columns of C
-    const int ldw = len | 1, ldv = ncol | 1;
-    const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(T);
-    T* Wm = (need <= (size_t)SM_WORK) ? work : scr + J.lay.jw_off;
-    T* Vm = (need <= (size_t)SM_WORK) ? work + (size_t)ncol * ldw : scr + J.lay.jv_off;
-    const int ldw_e = (need <= (size_t)SM_WORK) ? ldw : len;
-    const int ldv_e = (need <= (size_t)SM_WORK) ? ldv : ncol;
-    // scale by an exact power of two so that max |C| is in [1, 2): keeps the
-    // Jacobi inner products far from under- and overflow; undone exactly below
-    T amax = (T)0;
-    for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) amax = fmax(amax, fabs(C[idx]));
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)amax;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, s_red[w]);
-      int e = 0;
-      if (a > 0.0 && isfinite(a)) frexp(a, &e);
-      s_tau[1] = ldexp(1.0, 1 - e);     // scale
-    }
-    __syncthreads();
-    const double scl = s_tau[1];
-    const T tscl = (T)scl;
-    for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
-      const int jj = idx / len, i = idx % len;
-      Wm[(size_t)jj * ldw_e + i] = tscl * (trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]);
-    }
-    __syncthreads();
-    const int maxsw = 60;
-    pc.lap(PH_SVD_OUT);
-    int sw = jacobi_cols_hw<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
-    pc.lap(PH_JACOBI);
-    if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }   // sweeps, SVD count
-    if (sw >= maxsw && threadIdx.x == 0) {
-      flag(status, ST_NOCONV);
-      if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big
-        status[2] = blockIdx.x; status[3] = k; status[4] = ncol; status[5] = len;
-      }
-    }
-    for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
-      T a = (T)0;
-      const T* w = Wm + (size_t)jj * ldw_e;
-      for (int i = 0; i < len; ++i) a += w[i] * w[i];
-      s_sig[jj] = (double)sqrt(a) / scl;         // singular value of the unscaled C
-    }
-    __syncthreads();
-    for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
-      int rank = 0;
-      const double sj = s_sig[jj];
-      for (int o = 0; o < ncol; ++o) {
-        const double so = s_sig[o];
-        rank += (so > sj) || (so == sj && o < jj);
-      }
-      s_perm[rank] = jj;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // smallest r in [1, min(chi, ncol)] with discarded tail <= delta (FP64 tail)
-      const int rmax = imin(J.chi, ncol);
-      double tail2 = 0.0;
-      int r = rmax;
-      for (int p = ncol - 1; p >= 1; --p) {
-        const double sv = s_sig[s_perm[p]];
-        tail2 += sv * sv;
-        s_tau[2 + p] = tail2;                  // tail starting at position p
-      }
-      for (int rr = 1; rr <= rmax; ++rr) {
-        const double t2 = (rr < ncol) ? s_tau[2 + rr] : 0.0;
-        if (sqrt(t2) <= delta) { r = rr; break; }
-      }
-      if (r > bond_cap(L, J.dst.cap, k)) { s_bad = 1; r = bond_cap(L, J.dst.cap, k); }
-      s_rank = r;
-      flops += svd_flops(m, n);
-    }
-    __syncthreads();
-    if (s_bad) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
-    const int r = s_rank;
-    // outputs: core k = V^T[:r] (r x n) into dst; US (m x r) into scratch
     T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
     T* US = scr + J.lay.us_off;
-    for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) {
-      const int jr = idx / n, c = idx % n;
-      const int pj = s_perm[jr];
-      T v;
-      if (trans) {
-        v = Vm[(size_t)pj * ldv_e + c];
-      } else {
-        const T sg = (T)(s_sig[pj] * scl);       // norm of the scaled column
-        v = sg > (T)0 ? Wm[(size_t)pj * ldw_e + c] / sg : (T)(c == jr ? 1 : 0);
+    int r = 0;
+    bool done = false;
+    // ---- randomized truncation at a target rank, certified (learned-rank path)
+    int tgt = 0;
+    if (J.rsvd_mode && lc != nullptr && lc->omega != nullptr) {
+      if (J.rsvd_mode == 1) {
+        tgt = J.targets ? J.targets[k] : J.rsvd_k;
+      } else if (J.rsvd_mode == 3 && J.log != nullptr && J.log->valid[k]) {
+        tgt = J.log->label[k];                     // previous step's kept rank
+      } else if (J.rsvd_mode == 2 && lc->mlp != nullptr && J.log != nullptr && J.log->valid[k]) {
+        const float stepf = lc->step ? fminf((float)(*lc->step) / 1000.f, 1.f) : 0.f;
+        tgt = mlp_predict_rank(lc->mlp, J.log->spec[k], (float)k / (float)L, stepf, J.chi,
+                               (float*)s_sig);
       }
-      out[idx] = v;
     }
-    for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) {
-      const int i = idx / r, jr = idx % r;
-      const int pj = s_perm[jr];
-      US[idx] = trans ? Wm[(size_t)pj * ldw_e + i] * (T)(1.0 / scl)
-                      : Vm[(size_t)pj * ldv_e + i] * (T)s_sig[pj];
+    tgt = imin(tgt, J.chi);
+    const int fullmin = imin(m, n);
+    // at least TN_SPEC samples, so that the logged spectrum has every value the model reads
+    const int lsamp = imin(imax(tgt + (lc ? lc->oversample : 0), TN_SPEC), fullmin);
+    // Y (m x l, and n x l in the power steps) must fit the shared work area;
+    // B and V (l x n, l x l) go there too when they fit, else to global scratch
+    const bool fits = (size_t)imax(m, n) * (lsamp | 1) * sizeof(T) <= (size_t)SM_WORK;
+    const bool bv_smem = ((size_t)lsamp * (n | 1) + (size_t)lsamp * (lsamp | 1)) * sizeof(T) <= (size_t)SM_WORK;
+    if (tgt > 0 && lsamp < fullmin && fits && n <= lc->omega_rows && lsamp <= lc->omega_ld) {
+      const int l = lsamp;
+      const int ldy = l | 1, ldw = bv_smem ? (n | 1) : n, ldv = bv_smem ? (l | 1) : l;
+      T* Ysm = work;
+      const T* Om = (const T*)lc->omega;
+      // Y = C Omega (m x l), in shared memory
+      cta_gemm<T>(m, l, n, C, n, Om, lc->omega_ld, Ysm, ldy, false);
+      T* Qy = scr + J.lay.jw_off;                  // m x l
+      T* Rtmp = scr + J.lay.jv_off;                // l x l (discarded)
+      // power steps: Y <- C orth(C^T orth(Y)), re-orthonormalised for stability
+      for (int it = 0; it < lc->power; ++it) {
+        T* Z = scr + J.lay.rz_off;                 // n x l
+        householder_qr_par<T>(Ysm, m, l, ldy, Qy, l, Rtmp, l, s_tau, s_wv, s_red);
+        cta_gemm_tn<T>(n, l, m, C, n, Qy, l, Ysm, ldy);
+        householder_qr_par<T>(Ysm, n, l, ldy, Z, l, Rtmp, l, s_tau, s_wv, s_red);
+        cta_gemm<T>(m, l, n, C, n, Z, l, Ysm, ldy, false);
+        if (threadIdx.x == 0) flops += 4.0 * m * n * l + qr_flops(m, l) + qr_flops(n, l);
+      }
+      householder_qr_par<T>(Ysm, m, l, ldy, Qy, l, Rtmp, l, s_tau, s_wv, s_red);
+      // B = Qy^T C (l x n), row j = Jacobi column j; in shared memory, or in the
+      // power-step and R regions of the scratch (both free by now)
+      T* Wm = bv_smem ? work : scr + J.lay.rz_off;
+      T* Vm = bv_smem ? work + (size_t)l * ldw : Rtmp;
+      cta_gemm_tn<T>(l, n, m, Qy, l, C, n, Wm, ldw);
+      // residual ||C - Qy B||^2 and ||C||^2 (FP64 sums)
+      double pr = 0.0, pc2 = 0.0;
+      for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+        const int i = idx / n, c = idx % n;
+        const T* qrow = Qy + (size_t)i * l;
+        T acc = C[idx];
+        for (int q = 0; q < l; ++q) acc -= qrow[q] * Wm[(size_t)q * ldw + c];
+        pr += (double)acc * (double)acc;
+        pc2 += (double)C[idx] * (double)C[idx];
+      }
+      const double resid2 = block_sum(pr, s_red);
+      const double c2 = block_sum(pc2, s_red);
+      // scale B to max |entry| in [1, 2)
+      T amax = (T)0;
+      for (int idx = threadIdx.x; idx < l * n; idx += blockDim.x)
+        amax = fmax(amax, fabs(Wm[(size_t)(idx / n) * ldw + idx % n]));
+      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)amax;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, s_red[w]);
+        int e = 0;
+        if (a > 0.0 && isfinite(a)) frexp(a, &e);
+        s_tau[1] = ldexp(1.0, 1 - e);
+      }
+      __syncthreads();
+      const double scl = s_tau[1];
+      for (int idx = threadIdx.x; idx < l * n; idx += blockDim.x)
+        Wm[(size_t)(idx / n) * ldw + idx % n] *= (T)scl;
+      __syncthreads();
+      const int sw = jacobi_cols_hw<T>(Wm, ldw, Vm, ldv, l, n, 60);
+      for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
+        T a = (T)0;
+        const T* w = Wm + (size_t)jj * ldw;
+        for (int i = 0; i < n; ++i) a += w[i] * w[i];
+        s_sig[jj] = (double)sqrt(a) / scl;
+      }
+      __syncthreads();
+      for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
+        int rank = 0;
+        const double sj = s_sig[jj];
+        for (int o = 0; o < l; ++o) rank += (s_sig[o] > sj) || (s_sig[o] == sj && o < jj);
+        s_perm[rank] = jj;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const int rmax = imin(J.chi, l);
+        double tail2 = 0.0;
+        s_tau[2 + l] = 0.0;
+        for (int p = l - 1; p >= 0; --p) {
+          const double sv = s_sig[s_perm[p]];
+          tail2 += sv * sv;
+          s_tau[2 + p] = tail2;
+        }
+        int rr = rmax;
+        for (int q = 1; q <= rmax; ++q)
+          if (sqrt(resid2 + s_tau[2 + q]) <= delta) { rr = q; break; }
+        const double err2 = resid2 + s_tau[2 + rr];
+        const int full_cap = imin(J.chi, imin(m, n));
+        const bool rule_ok = sqrt(err2) <= delta || rr == full_cap || rr == J.chi;
+        // accept: measured error within the tolerance, or (at the chi cap) the
+        // residual bound proves err^2 <= opt^2 / (1 - eta) (Ky Fan on C^T C = B^T B + E^T E)
+        const double floor2 = (double)lc->floor_rel * (double)lc->floor_rel * c2;
+        const bool cert = sqrt(err2) <= delta || resid2 <= fmax((double)lc->eta * err2, floor2);
+        const bool ok = rule_ok && cert && sw < 60 && rr <= bond_cap(L, J.dst.cap, k);
+        s_rank = ok ? rr : 0;
+        if (lc->counters) atomicAdd(&lc->counters[ok ? 0 : 1], 1);
+        flops += 2.0 * m * n * l * 3 + qr_flops(m, l) + svd_flops(l, n);
+      }
+      __syncthreads();
+      if (s_rank > 0) {
+        r = s_rank;
+        for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) {
+          const int jr = idx / n, c = idx % n;
+          const int pj = s_perm[jr];
+          const T sg = (T)(s_sig[pj] * scl);
+          out[idx] = sg > (T)0 ? Wm[(size_t)pj * ldw + c] / sg : (T)(c == jr ? 1 : 0);
+        }
+        for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) {
+          const int i = idx / r, jr = idx % r;
+          const int pj = s_perm[jr];
+          const T* qrow = Qy + (size_t)i * l;
+          const T* vcol = Vm + (size_t)pj * ldv;
+          T acc = (T)0;
+          for (int q = 0; q < l; ++q) acc += qrow[q] * vcol[q];
+          US[idx] = acc * (T)s_sig[pj];
+        }
+        done = true;
+        if (threadIdx.x == 0) J.dst.ranks[k] = r;
+      }
+      __syncthreads();
+      pc.lap(PH_JACOBI);
     }
-    if (threadIdx.x == 0) J.dst.ranks[k] = r;
+    // ---- full SVD (reference path, and fallback of the randomized one)
+    const int ncol = imin(m, n), len = imax(m, n);
+    if (!done) {
+      if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+      const bool trans = (n <= m);             // Jacobi on the columns of C
+      const int ldw = len | 1, ldv = ncol | 1;
+      const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(T);
+      T* Wm = (need <= (size_t)SM_WORK) ? work : scr + J.lay.jw_off;
+      T* Vm = (need <= (size_t)SM_WORK) ? work + (size_t)ncol * ldw : scr + J.lay.jv_off;
+      const int ldw_e = (need <= (size_t)SM_WORK) ? ldw : len;
+      const int ldv_e = (need <= (size_t)SM_WORK) ? ldv : ncol;
+      // scale by an exact power of two so that max |C| is in [1, 2): keeps the
+      // Jacobi inner products far from under- and overflow; undone exactly below
+      T amax = (T)0;
+      for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) amax = fmax(amax, fabs(C[idx]));
+      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = (double)amax;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, s_red[w]);
+        int e = 0;
+        if (a > 0.0 && isfinite(a)) frexp(a, &e);
+        s_tau[1] = ldexp(1.0, 1 - e);     // scale
+      }
+      __syncthreads();
+      const double scl = s_tau[1];
+      const T tscl = (T)scl;
+      for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
+        const int jj = idx / len, i = idx % len;
+        Wm[(size_t)jj * ldw_e + i] = tscl * (trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]);
+      }
+      __syncthreads();
+      const int maxsw = 60;
+      pc.lap(PH_SVD_OUT);
+      int sw = jacobi_cols_hw<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
+      pc.lap(PH_JACOBI);
+      if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }   // sweeps, SVD count
+      if (sw >= maxsw && threadIdx.x == 0) {
+        flag(status, ST_NOCONV);
+        if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big
+          status[2] = blockIdx.x; status[3] = k; status[4] = ncol; status[5] = len;
+        }
+      }
+      for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+        T a = (T)0;
+        const T* w = Wm + (size_t)jj * ldw_e;
+        for (int i = 0; i < len; ++i) a += w[i] * w[i];
+        s_sig[jj] = (double)sqrt(a) / scl;         // singular value of the unscaled C
+      }
+      __syncthreads();
+      for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+        int rank = 0;
+        const double sj = s_sig[jj];
+        for (int o = 0; o < ncol; ++o) {
+          const double so = s_sig[o];
+          rank += (so > sj) || (so == sj && o < jj);
+        }
+        s_perm[rank] = jj;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        // smallest r in [1, min(chi, ncol)] with discarded tail <= delta (FP64 tail)
+        const int rmax = imin(J.chi, ncol);
+        double tail2 = 0.0;
+        int rr = rmax;
+        for (int p = ncol - 1; p >= 1; --p) {
+          const double sv = s_sig[s_perm[p]];
+          tail2 += sv * sv;
+          s_tau[2 + p] = tail2;                  // tail starting at position p
+        }
+        for (int q = 1; q <= rmax; ++q) {
+          const double t2 = (q < ncol) ? s_tau[2 + q] : 0.0;
+          if (sqrt(t2) <= delta) { rr = q; break; }
+        }
+        if (rr > bond_cap(L, J.dst.cap, k)) { s_bad = 1; rr = bond_cap(L, J.dst.cap, k); }
+        s_rank = rr;
+        flops += svd_flops(m, n);
+        if (lc && lc->counters) atomicAdd(&lc->counters[2], 1);
+      }
+      __syncthreads();
+      if (s_bad) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+      r = s_rank;
+      // outputs: core k = V^T[:r] (r x n) into dst; US (m x r) into scratch
+      for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) {
+        const int jr = idx / n, c = idx % n;
+        const int pj = s_perm[jr];
+        T v;
+        if (trans) {
+          v = Vm[(size_t)pj * ldv_e + c];
+        } else {
+          const T sg = (T)(s_sig[pj] * scl);       // norm of the scaled column
+          v = sg > (T)0 ? Wm[(size_t)pj * ldw_e + c] / sg : (T)(c == jr ? 1 : 0);
+        }
+        out[idx] = v;
+      }
+      for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) {
+        const int i = idx / r, jr = idx % r;
+        const int pj = s_perm[jr];
+        US[idx] = trans ? Wm[(size_t)pj * ldw_e + i] * (T)(1.0 / scl)
+                        : Vm[(size_t)pj * ldv_e + i] * (T)s_sig[pj];
+      }
+      if (threadIdx.x == 0) J.dst.ranks[k] = r;
+      __syncthreads();
+    }
+    // ---- sign gauge of the kept singular pairs: each row of V^T gets a
+    // positive inner product with the probe weights frac((c+1) g) + 1/4,
+    // g = 0.618..., a generic positive vector (rows with tied entries are
+    // common in structured fields).  Contracted results do not depend on the
+    // gauge; the randomized sample of the next step does.
     __syncthreads();
+    {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int jr = warp; jr < r; jr += nw) {
+        T* row = out + (size_t)jr * n;
+        double dot = 0.0;
+        for (int c = lane; c < n; c += 32) {
+          const double x = (double)(c + 1) * 0.6180339887498949;
+          dot += (double)row[c] * (x - floor(x) + 0.25);
+        }
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        __syncwarp();
+        if (dot < 0.0) {
+          for (int c = lane; c < n; c += 32) row[c] = -row[c];
+          for (int i = lane; i < m; i += 32) US[(size_t)i * r + jr] = -US[(size_t)i * r + jr];
+        }
+      }
+    }
+    __syncthreads();
+    // ---- spectrum log: (features of the previous step, rank kept now)
+    if (J.log != nullptr && lc != nullptr) {
+      const int nsv = done ? imin(lsamp, TN_SPEC) : imin(ncol, TN_SPEC);
+      if (threadIdx.x == 0 && lc->dataset != nullptr && J.log->valid[k]) {
+        const int slot = atomicAdd(lc->dataset_count, 1);
+        if (slot < lc->dataset_cap) {
+          float* row = lc->dataset + (size_t)slot * (MLP_IN + 1);
+          for (int q = 0; q < TN_SPEC; ++q) row[q] = J.log->spec[k][q];
+          row[16] = (float)k / (float)L;
+          row[17] = lc->step ? fminf((float)(*lc->step) / 1000.f, 1.f) : 0.f;
+          row[18] = (float)r / (float)J.chi;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < TN_SPEC) {
+        const double s0 = s_sig[s_perm[0]];
+        const double sv = threadIdx.x < nsv ? s_sig[s_perm[threadIdx.x]] : 0.0;
+        J.log->spec[k][threadIdx.x] = (s0 > 0.0 && sv > 0.0) ? (float)log10(fmax(sv / s0, 1e-20)) : -20.f;
+      }
+      if (threadIdx.x == 0) { J.log->label[k] = r; J.log->valid[k] = 1; }
+      __syncthreads();
+    }
     // C' = Q_{k-1} (2 q_{k-1} x m) * US (m x r)
     const int rows = 2 * s_q[k - 1];
     const T* Qp = scr + J.lay.q_off[k - 1];
@@ -478,7 +675,8 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
 
 template <typename T>
 void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T* d_masks,
-                  const double* d_scal, int* d_status, cudaStream_t st, double* d_ctr) {
+                  const double* d_scal, int* d_status, cudaStream_t st, double* d_ctr,
+                  const LearnCtx* d_learn) {
   if (njobs <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
@@ -487,12 +685,12 @@ void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T*
     attr_set = true;
   }
   round_kernel<T><<<njobs, RT, round_smem_bytes(), st>>>(d_jobs, L, n_bits, d_masks, d_scal,
-                                                         d_status, d_ctr);
+                                                         d_status, d_ctr, d_learn);
 }
 
 template void launch_round<float>(const RoundJob*, int, int, int, const float*, const double*,
-                                  int*, cudaStream_t, double*);
+                                  int*, cudaStream_t, double*, const LearnCtx*);
 template void launch_round<double>(const RoundJob*, int, int, int, const double*,
-                                   const double*, int*, cudaStream_t, double*);
+                                   const double*, int*, cudaStream_t, double*, const LearnCtx*);
 
 }  // namespace tn

@@ -138,6 +138,101 @@ def lincomb_round_noalloc(batches, dst, chi_max, eps, stream=None):
     nat.check(rc, "tnlbm_lincomb_round_noalloc")
 
 
+def lincomb_round_rsvd(batches, dst, chi_max, eps, targets, omega, oversample=8, power=1, eta=0.2,
+                       floor_rel=1e-12, stream=None):
+    """lincomb_round with the certified randomized truncation at target ranks
+    (tnlbm_lincomb_round_rsvd).  targets: (batch, L + 1) ints, 0 = full SVD;
+    omega: device tensor (rows x ld) of the rounding's type.  Returns the
+    counts (accepted, fell back, full SVDs)."""
+    arr, nterms, keep = _terms_array(batches)
+    p = dst[0].precision
+    L = dst[0].L
+    tg = np.ascontiguousarray(np.asarray(targets, dtype=np.int32).reshape(len(dst), L + 1))
+    if omega.dtype != (torch.float64 if p == nat.FP64 else torch.float32) or not omega.is_contiguous():
+        raise ValueError("omega must be a contiguous tensor of the rounding's type")
+    cnt = (ctypes.c_int * 3)()
+    rc = nat.lib().tnlbm_lincomb_round_rsvd(p, L // 3, len(dst), nterms, arr,
+                                            _ptrs([d.data for d in dst]), _ptrs([d.ranks for d in dst]),
+                                            dst[0].cap, chi_max, eps, tg.ctypes.data_as(nat.c_int_p),
+                                            ctypes.c_void_p(omega.data_ptr()), omega.shape[0], omega.shape[1],
+                                            oversample, power, eta, floor_rel, cnt, _stream(stream))
+    nat.check(rc, "tnlbm_lincomb_round_rsvd")
+    return tuple(cnt)
+
+
+# ---------------------------------------------------------------- rank model
+MLP_IN = 18
+MLP_H = 64
+
+
+def mlp_param_count():
+    return nat.lib().tnlbm_mlp_param_count()
+
+
+def mlp_flatten(P):
+    """Dict of arrays (W1, b1, W2, b2, W3, b3) -> flat float32 vector in the
+    library's layout."""
+    return np.concatenate([np.asarray(P[k], dtype=np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+def mlp_unflatten(v):
+    v = np.asarray(v, dtype=np.float64)
+    shapes = [("W1", (MLP_H, MLP_IN)), ("b1", (MLP_H,)), ("W2", (MLP_H, MLP_H)), ("b2", (MLP_H,)),
+              ("W3", (1, MLP_H)), ("b3", (1,))]
+    out, o = {}, 0
+    for k, sh in shapes:
+        n = int(np.prod(sh))
+        out[k] = v[o:o + n].reshape(sh)
+        o += n
+    return out
+
+
+def _f32(t):
+    if t.dtype != torch.float32 or not t.is_contiguous() or t.device.type != "cuda":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mlp_forward(params, X, stream=None):
+    """Predictions (M,) of the rank model for features X (M x 18); params is the
+    flat FP32 device vector."""
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    nat.check(nat.lib().tnlbm_mlp_forward(_f32(params), X.shape[0], _f32(X), _f32(out), _stream(stream)),
+              "tnlbm_mlp_forward")
+    return out
+
+
+def mlp_loss_grad(params, X, y, stream=None):
+    """(mean squared error, gradient) for the flat FP32 device parameters."""
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    grad = torch.zeros_like(params)
+    nat.check(nat.lib().tnlbm_mlp_loss_grad(_f32(params), X.shape[0], _f32(X), _f32(y), _f32(loss),
+                                            _f32(grad), _stream(stream)), "tnlbm_mlp_loss_grad")
+    return loss, grad
+
+
+class MlpTrainer:
+    """FP32 master parameters with Adam state, trained by tnlbm_mlp_train; the
+    FP16 copy (`half`) is what a simulation evaluates."""
+
+    def __init__(self, params):
+        self.master = params.detach().clone().contiguous()
+        self.m = torch.zeros_like(self.master)
+        self.v = torch.zeros_like(self.master)
+        self.half = self.master.to(torch.float16)
+        self.t = 0
+
+    def train(self, X, y, iters, batch=256, lr=1e-3, stream=None):
+        hist = torch.zeros(max(iters, 1), dtype=torch.float32, device=X.device)
+        rc = nat.lib().tnlbm_mlp_train(_f32(self.master), _f32(self.m), _f32(self.v),
+                                       ctypes.c_void_p(self.half.data_ptr()), X.shape[0], _f32(X), _f32(y),
+                                       iters, batch, self.t, lr, _f32(hist), _stream(stream))
+        nat.check(rc, "tnlbm_mlp_train")
+        self.t += iters
+        return hist[:iters]
+
+
 def materialize(terms, dst, stream=None):
     arr, _, keep = _terms_array([[t] for t in terms])
     p = dst[0].precision
@@ -300,6 +395,40 @@ class Sim:
         out = {c: dict(ms=ms[i], flops=fl[i], launches=la[i]) for i, c in enumerate(nat.KERNEL_CLASSES)}
         out["round"]["phase_cycles"] = {p: ph[i] for i, p in enumerate(nat.ROUND_PHASES)}
         return out
+
+    def learn_configure(self, mode, omega, oversample=8, power=1, eta=0.2, floor_rel=None, dataset_cap=0):
+        """Learned rounding: mode 0 off, 1 log spectra, 2 rank model + randomized
+        truncation, 3 previous step's rank + randomized truncation
+        (tnlbm_learn_configure).  omega: host array (rows x ld)."""
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        if floor_rel is None:
+            floor_rel = 1e-12 if self.cfg.precision == nat.FP64 else 1e-5
+        nat.check(nat.lib().tnlbm_learn_configure(self.h, mode, om.ctypes.data_as(nat.c_double_p), om.shape[0],
+                                                  om.shape[1], oversample, power, eta, floor_rel, dataset_cap),
+                  "tnlbm_learn_configure")
+
+    def learn_set_mlp(self, half_params):
+        """half_params: FP16 tensor (device or host) of mlp_param_count() values."""
+        t = half_params.contiguous()
+        if t.dtype != torch.float16 or t.numel() != mlp_param_count():
+            raise ValueError("expected the FP16 parameter vector of the rank model")
+        nat.check(nat.lib().tnlbm_learn_set_mlp(self.h, ctypes.c_void_p(t.data_ptr())), "tnlbm_learn_set_mlp")
+
+    def learn_dataset(self, cap, reset=False):
+        """(features (n x 18), labels (n,)) logged so far, at most cap rows; and
+        the total number of rows logged."""
+        out = np.zeros((max(cap, 1), MLP_IN + 1), dtype=np.float32)
+        cnt = ctypes.c_int()
+        nat.check(nat.lib().tnlbm_learn_dataset(self.h, out.ctypes.data_as(ctypes.c_void_p), cap,
+                                                ctypes.byref(cnt), int(reset)), "tnlbm_learn_dataset")
+        n = min(cnt.value, cap)
+        return out[:n, :MLP_IN].copy(), out[:n, MLP_IN].copy(), cnt.value
+
+    def learn_counters(self, reset=False):
+        """(randomized accepted, fell back, full SVDs) since configure / reset."""
+        out = (ctypes.c_longlong * 3)()
+        nat.check(nat.lib().tnlbm_learn_counters(self.h, out, int(reset)), "tnlbm_learn_counters")
+        return tuple(out)
 
     def stats(self):
         s = nat.Stats()
