@@ -235,6 +235,32 @@ int tnlbm_from_dense(int precision, int n_bits, const void *dense, void *dst,
                      int *dst_ranks, int dst_cap, int chi_max, double eps,
                      void *stream);
 
+/* ------------------------------------------------------------------ batched simulations
+ * Several independent simulations (same n_per_axis, precision and fit sweeps;
+ * lattice, geometry, walls, tau, force, chi, eps and start may differ) stepped
+ * together: each dependency level of the step (Sec. 3.2) launches the
+ * roundings and fits of that level of every simulation at once, and one CUDA
+ * graph holds the whole batched step.  The paper runs one simulation at a
+ * time; results are bitwise those of the simulations stepped alone. */
+typedef struct tnlbm_batch tnlbm_batch; /* opaque; owns its simulations */
+
+/* Creates cfgs[0..nsim) (1 <= nsim <= 64) as for tnlbm_create.  On error no
+ * simulation is left allocated. */
+int tnlbm_batch_create(const tnlbm_config *cfgs, int nsim, tnlbm_batch **out);
+/* k batched steps; synchronous; device status checked after the last. */
+int tnlbm_batch_step(tnlbm_batch *b, int k);
+/* k batched steps timed with CUDA events on the batch's stream (ms). */
+int tnlbm_batch_step_timed(tnlbm_batch *b, int k, double *ms);
+/* Borrowed handle of simulation i (owned by the batch: never destroy it).
+ * tnlbm_macroscopic / get / set populations / stats work on it between
+ * batched steps; stepping it alone is allowed too.  NULL on bad arguments. */
+tnlbm_sim *tnlbm_batch_sim(tnlbm_batch *b, int i);
+/* Simulations, kernel launches per batched step, jobs (roundings + fits) per
+ * batched step; any pointer may be NULL. */
+int tnlbm_batch_info(tnlbm_batch *b, int *nsim, int *launches_per_step,
+                     int *jobs_per_step);
+int tnlbm_batch_destroy(tnlbm_batch *b);
+
 /* ------------------------------------------------------------------ learned rounding
  * Not part of the paper: the full SVD of each right-to-left step of the
  * rounding (Eq. svd-move) may be replaced by a randomized truncation at a

@@ -1420,3 +1420,239 @@ int tnlbm_profile_step(tnlbm_sim* s, double* ms, double* flops, int* launches, d
 }
 
 }  // extern "C"
+
+// ================================================================ batched simulations
+// Several independent simulations of the same lattice size stepped together:
+// level l of the step launches the roundings and fits of level l of every
+// simulation at once (each job carries its own simulation's masks, scalars and
+// scratch), so that a launch holds the jobs of all of them.
+struct tnlbm_batch {
+  std::vector<tnlbm_sim*> sims;
+  int prec = 0, n = 0, L = 0, sweeps = 2;
+  Arena arena;
+  cudaStream_t s0 = nullptr, s1 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  struct Level {
+    std::vector<RoundJob> rj;
+    std::vector<FitJob> fj;
+    RoundJob* d_rj = nullptr;
+    FitJob* d_fj = nullptr;
+    std::vector<int> rho0;       // simulations with a rho_0 node at this level
+  };
+  std::vector<Level> levels;
+  int* d_status = nullptr;
+  MpsRef* d_copy_src = nullptr;
+  MpsRef* d_copy_dst = nullptr;
+  int ncopy = 0;
+  int launches_per_step = 0;
+};
+
+namespace tn {
+
+template <typename T>
+static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
+  int nl = 0;
+  for (auto& lv : b->levels) {
+    for (int si : lv.rho0) {
+      tnlbm_sim* s = b->sims[si];
+      launch_rho0<T>(s->d_rho_ref, b->L, s->n_fluid, s->d_scal, b->s0);
+      ++nl;
+    }
+    const bool both = !lv.rj.empty() && !lv.fj.empty();
+    if (both) {
+      cudaEventRecord(b->ev_fork, b->s0);
+      cudaStreamWaitEvent(b->s1, b->ev_fork, 0);
+    }
+    if (!lv.fj.empty())
+      nl += run_fit<T>(lv.d_fj, lv.fj, b->L, b->sweeps, b->d_status, both ? b->s1 : b->s0, nullptr);
+    if (!lv.rj.empty()) {
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->L, b->n, nullptr, nullptr, b->d_status, b->s0);
+      ++nl;
+    }
+    if (both) {
+      cudaEventRecord(b->ev_join, b->s1);
+      cudaStreamWaitEvent(b->s0, b->ev_join, 0);
+    }
+  }
+  for (tnlbm_sim* s : b->sims)
+    if (s->cfg.conserve_mass) {
+      launch_mass_fix<T>(s->d_copy_src, s->lat.Q, b->L, s->d_mass, s->d_mass0, b->s0);
+      nl += 2;
+    }
+  launch_copy<T>(b->d_copy_src, b->d_copy_dst, b->ncopy, b->L, b->s0);
+  ++nl;
+  *launches = nl;
+  return 0;
+}
+
+template <typename T>
+static int batch_build(tnlbm_batch* b) {
+  TN_CUDA(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
+  TN_CUDA(cudaStreamCreateWithFlags(&b->s1, cudaStreamNonBlocking));
+  TN_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  TN_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  b->d_status = (int*)b->arena.alloc(STATUS_INTS * sizeof(int));
+  if (!b->d_status) return TNLBM_E_OOM;
+  TN_CUDA(cudaMemset(b->d_status, 0, STATUS_INTS * sizeof(int)));
+  size_t nlev = 0;
+  for (tnlbm_sim* s : b->sims) nlev = std::max(nlev, s->levels.size());
+  b->levels.assign(nlev, tnlbm_batch::Level{});
+  std::vector<MpsRef> src, dst;
+  for (int si = 0; si < (int)b->sims.size(); ++si) {
+    tnlbm_sim* s = b->sims[si];
+    for (size_t l = 0; l < s->levels.size(); ++l) {
+      auto& in = s->levels[l];
+      auto& out = b->levels[l];
+      for (RoundJob rj : in.rj) {
+        rj.masks = s->d_masks;
+        rj.scal = s->d_scal;
+        out.rj.push_back(rj);
+      }
+      for (const FitJob& fj : in.fj) out.fj.push_back(fj);
+      if (in.has_rho0) out.rho0.push_back(si);
+    }
+    for (int i = 0; i < s->lat.Q; ++i) {
+      src.push_back(s->nodes[s->f_next[i]]);
+      dst.push_back(s->nodes[s->f_state[i]]);
+    }
+  }
+  for (auto& lv : b->levels) {
+    if (!lv.rj.empty()) {
+      lv.d_rj = (RoundJob*)b->arena.alloc(lv.rj.size() * sizeof(RoundJob));
+      if (!lv.d_rj) return TNLBM_E_OOM;
+      TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
+    }
+    if (!lv.fj.empty()) {
+      lv.d_fj = (FitJob*)b->arena.alloc(lv.fj.size() * sizeof(FitJob));
+      if (!lv.d_fj) return TNLBM_E_OOM;
+      TN_CUDA(cudaMemcpy(lv.d_fj, lv.fj.data(), lv.fj.size() * sizeof(FitJob), cudaMemcpyHostToDevice));
+    }
+  }
+  b->ncopy = (int)src.size();
+  b->d_copy_src = (MpsRef*)b->arena.alloc(src.size() * sizeof(MpsRef));
+  b->d_copy_dst = (MpsRef*)b->arena.alloc(dst.size() * sizeof(MpsRef));
+  if (!b->d_copy_src || !b->d_copy_dst) return TNLBM_E_OOM;
+  TN_CUDA(cudaMemcpy(b->d_copy_src, src.data(), src.size() * sizeof(MpsRef), cudaMemcpyHostToDevice));
+  TN_CUDA(cudaMemcpy(b->d_copy_dst, dst.data(), dst.size() * sizeof(MpsRef), cudaMemcpyHostToDevice));
+  TN_CUDA(cudaDeviceSynchronize());
+  TN_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  enqueue_batch_step<T>(b, &launches);
+  TN_CUDA(cudaStreamEndCapture(b->s0, &b->graph));
+  TN_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  b->launches_per_step = launches;
+  return 0;
+}
+
+static int batch_status(tnlbm_batch* b) {
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, b->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (st[0]) {
+    cudaMemset(b->d_status, 0, sizeof(st));
+    return status_to_code(st);
+  }
+  return 0;
+}
+
+}  // namespace tn
+
+extern "C" {
+
+int tnlbm_batch_destroy(tnlbm_batch* b) {
+  if (!b) return 0;
+  if (b->s0) cudaStreamSynchronize(b->s0);
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->s0) cudaStreamDestroy(b->s0);
+  if (b->s1) cudaStreamDestroy(b->s1);
+  for (tnlbm_sim* s : b->sims) tnlbm_destroy(s);
+  delete b;
+  return 0;
+}
+
+int tnlbm_batch_create(const tnlbm_config* cfgs, int nsim, tnlbm_batch** out) {
+  if (!out) { set_error("out is NULL"); return TNLBM_E_ARG; }
+  *out = nullptr;
+  if (!cfgs || nsim < 1 || nsim > 64) { set_error("bad arguments to tnlbm_batch_create"); return TNLBM_E_ARG; }
+  for (int i = 1; i < nsim; ++i)
+    if (cfgs[i].n_per_axis != cfgs[0].n_per_axis || cfgs[i].precision != cfgs[0].precision ||
+        std::max(cfgs[i].sweeps, 0) != std::max(cfgs[0].sweeps, 0)) {
+      set_error("batched simulations need the same n_per_axis, precision and fit sweeps");
+      return TNLBM_E_ARG;
+    }
+  tnlbm_batch* b = new (std::nothrow) tnlbm_batch();
+  if (!b) { set_error("host allocation failed"); return TNLBM_E_OOM; }
+  for (int i = 0; i < nsim; ++i) {
+    tnlbm_sim* s = nullptr;
+    int rc = tnlbm_create(&cfgs[i], &s);
+    if (rc) {
+      std::string msg = tn::g_err;
+      tnlbm_batch_destroy(b);
+      tn::g_err = "simulation " + std::to_string(i) + " of the batch: " + msg;
+      return rc;
+    }
+    b->sims.push_back(s);
+  }
+  b->n = b->sims[0]->n;
+  b->L = b->sims[0]->L;
+  b->prec = b->sims[0]->prec;
+  b->sweeps = b->sims[0]->cfg.sweeps;
+  int rc = b->prec == TNLBM_FP64 ? tn::batch_build<double>(b) : tn::batch_build<float>(b);
+  if (rc) {
+    std::string msg = tn::g_err;
+    tnlbm_batch_destroy(b);
+    tn::g_err = msg;
+    return rc;
+  }
+  *out = b;
+  return 0;
+}
+
+int tnlbm_batch_step(tnlbm_batch* b, int k) {
+  if (!b || k < 0) { set_error("bad arguments to tnlbm_batch_step"); return TNLBM_E_ARG; }
+  for (int i = 0; i < k; ++i) TN_CUDA(cudaGraphLaunch(b->gexec, b->s0));
+  TN_CUDA(cudaStreamSynchronize(b->s0));
+  for (tnlbm_sim* s : b->sims) s->steps += k;
+  return tn::batch_status(b);
+}
+
+int tnlbm_batch_step_timed(tnlbm_batch* b, int k, double* ms) {
+  if (!b || k < 0 || !ms) { set_error("bad arguments to tnlbm_batch_step_timed"); return TNLBM_E_ARG; }
+  cudaEvent_t e0, e1;
+  TN_CUDA(cudaEventCreate(&e0));
+  TN_CUDA(cudaEventCreate(&e1));
+  TN_CUDA(cudaEventRecord(e0, b->s0));
+  for (int i = 0; i < k; ++i) TN_CUDA(cudaGraphLaunch(b->gexec, b->s0));
+  TN_CUDA(cudaEventRecord(e1, b->s0));
+  TN_CUDA(cudaEventSynchronize(e1));
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t;
+  for (tnlbm_sim* s : b->sims) s->steps += k;
+  return tn::batch_status(b);
+}
+
+tnlbm_sim* tnlbm_batch_sim(tnlbm_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->sims.size()) { set_error("bad arguments to tnlbm_batch_sim"); return nullptr; }
+  return b->sims[i];
+}
+
+int tnlbm_batch_info(tnlbm_batch* b, int* nsim, int* launches_per_step, int* jobs_per_step) {
+  if (!b) { set_error("bad arguments to tnlbm_batch_info"); return TNLBM_E_ARG; }
+  if (nsim) *nsim = (int)b->sims.size();
+  if (launches_per_step) *launches_per_step = b->launches_per_step;
+  if (jobs_per_step) {
+    int j = 0;
+    for (auto& lv : b->levels) j += (int)(lv.rj.size() + lv.fj.size());
+    *jobs_per_step = j;
+  }
+  return 0;
+}
+
+}  // extern "C"

@@ -119,6 +119,12 @@ SIGNATURES = {
     "tnlbm_learn_dataset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, c_int_p,
                                            ctypes.c_int]),
     "tnlbm_learn_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]),
+    "tnlbm_batch_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    "tnlbm_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "tnlbm_batch_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
+    "tnlbm_batch_sim": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int]),
+    "tnlbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p]),
+    "tnlbm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tnlbm_materialize": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Term),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.c_int, ctypes.c_void_p]),

@@ -282,61 +282,80 @@ def from_dense(dense, cap, chi_max, eps, stream=None):
     return X
 
 
+def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
+                chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
+                eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
+                conserve_mass=False):
+    """tnlbm_config for the arguments; returns (config, arrays the config
+    points to, which must stay alive until the simulation is created)."""
+    c = nat.Config()
+    c.n_per_axis = n_per_axis
+    c.lattice = lattice
+    c.tau = tau
+    for d in range(3):
+        c.periodic[d] = int(periodic[d])
+        c.force[d] = float(force[d])
+    keep = []
+    if solid is not None:
+        sv = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        keep.append(sv)
+        c.solid = sv.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    c.chi_mask = chi_mask
+    c.eps_mask = eps_mask
+    if mask_cores is not None:
+        L = len(mask_cores)
+        r = [1] + [x.shape[2] for x in mask_cores]
+        cap = max(r)
+        flat = np.zeros(mps_size(L, cap))
+        for k, x in enumerate(mask_cores):
+            o = mps_offset(L, cap, k)
+            flat[o:o + x.size] = x.reshape(-1)
+        rr = np.array(r, dtype=np.int32)
+        keep += [flat, rr]
+        c.mask_cores = flat.ctypes.data_as(nat.c_double_p)
+        c.mask_ranks = rr.ctypes.data_as(nat.c_int_p)
+        c.mask_cap = cap
+    c.chi_max = chi_max
+    c.eps = eps
+    c.precision = precision
+    c.hadamard = hadamard
+    c.sweeps = sweeps
+    c.conserve_mass = int(bool(conserve_mass))
+    if modes is not None:
+        m = np.ascontiguousarray(modes, dtype=np.float64)
+        keep.append(m)
+        c.n_modes = m.shape[0]
+        c.modes = m.ctypes.data_as(nat.c_double_p)
+    return c, keep
+
+
 class Sim:
     """Handle of a tnlbm_sim (tnlbm_create ... tnlbm_destroy)."""
 
-    def __init__(self, n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
-                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
-                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
-                 conserve_mass=False):
-        c = nat.Config()
-        c.n_per_axis = n_per_axis
-        c.lattice = lattice
-        c.tau = tau
-        for d in range(3):
-            c.periodic[d] = int(periodic[d])
-            c.force[d] = float(force[d])
-        self._keep = []
-        if solid is not None:
-            s = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
-            self._keep.append(s)
-            c.solid = s.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
-        c.chi_mask = chi_mask
-        c.eps_mask = eps_mask
-        if mask_cores is not None:
-            L = len(mask_cores)
-            r = [1] + [x.shape[2] for x in mask_cores]
-            cap = max(r)
-            flat = np.zeros(mps_size(L, cap))
-            for k, x in enumerate(mask_cores):
-                o = mps_offset(L, cap, k)
-                flat[o:o + x.size] = x.reshape(-1)
-            rr = np.array(r, dtype=np.int32)
-            self._keep += [flat, rr]
-            c.mask_cores = flat.ctypes.data_as(nat.c_double_p)
-            c.mask_ranks = rr.ctypes.data_as(nat.c_int_p)
-            c.mask_cap = cap
-        c.chi_max = chi_max
-        c.eps = eps
-        c.precision = precision
-        c.hadamard = hadamard
-        c.sweeps = sweeps
-        c.conserve_mass = int(bool(conserve_mass))
-        if modes is not None:
-            m = np.ascontiguousarray(modes, dtype=np.float64)
-            self._keep.append(m)
-            c.n_modes = m.shape[0]
-            c.modes = m.ctypes.data_as(nat.c_double_p)
-        self.cfg = c
-        self.n = n_per_axis
-        self.N = 1 << n_per_axis
-        self.L = 3 * n_per_axis
-        self.Q = lattice
-        self.chi = chi_max
+    def __init__(self, n_per_axis, **kw):
+        c, keep = make_config(n_per_axis, **kw)
+        self._init_fields(c)
         h = ctypes.c_void_p()
         nat.check(nat.lib().tnlbm_create(ctypes.byref(c), ctypes.byref(h)), "tnlbm_create")
         self.h = h
-        self._keep = []
+        self._owned = True
+        del keep
+
+    def _init_fields(self, c):
+        self.cfg = c
+        self.n = c.n_per_axis
+        self.N = 1 << c.n_per_axis
+        self.L = 3 * c.n_per_axis
+        self.Q = c.lattice
+        self.chi = c.chi_max
+
+    @classmethod
+    def _borrowed(cls, handle, c):
+        obj = cls.__new__(cls)
+        obj._init_fields(c)
+        obj.h = ctypes.c_void_p(handle)
+        obj._owned = False
+        return obj
 
     def step(self, k=1):
         nat.check(nat.lib().tnlbm_step(self.h, k), "tnlbm_step")
@@ -437,7 +456,50 @@ class Sim:
 
     def close(self):
         if getattr(self, "h", None):
-            nat.lib().tnlbm_destroy(self.h)
+            if getattr(self, "_owned", True):
+                nat.lib().tnlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several simulations of the same lattice size stepped together
+    (tnlbm_batch_create ... tnlbm_batch_destroy).  configs: list of keyword
+    dicts for make_config (each with n_per_axis)."""
+
+    def __init__(self, configs):
+        made = [make_config(**kw) for kw in configs]
+        arr = (nat.Config * len(made))(*[c for c, _ in made])
+        h = ctypes.c_void_p()
+        nat.check(nat.lib().tnlbm_batch_create(arr, len(made), ctypes.byref(h)), "tnlbm_batch_create")
+        self.h = h
+        self.sims = [Sim._borrowed(nat.lib().tnlbm_batch_sim(h, i), c) for i, (c, _) in enumerate(made)]
+        del made
+
+    def step(self, k=1):
+        nat.check(nat.lib().tnlbm_batch_step(self.h, k), "tnlbm_batch_step")
+
+    def step_timed(self, k=1):
+        ms = ctypes.c_double()
+        nat.check(nat.lib().tnlbm_batch_step_timed(self.h, k, ctypes.byref(ms)), "tnlbm_batch_step_timed")
+        return ms.value
+
+    def info(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nat.check(nat.lib().tnlbm_batch_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                  "tnlbm_batch_info")
+        return dict(sims=a.value, launches_per_step=b.value, jobs_per_step=c.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for s in self.sims:
+                s.h = None
+            nat.lib().tnlbm_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
