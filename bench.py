@@ -15,6 +15,8 @@ Prints one JSON line (rank 0):
   roofline   dominant kernel class of one profiled step against its peak
   cpu_baseline  the CPU oracle on a bounded sample of the same step
   clocks     nvidia-smi samples taken during the timed region
+  batched    eight 64^3 simulations stepped in one graph, against the same
+             eight one after another and one plain FP64 full-SVD simulation
 
 --impl reference times the CPU oracle instead (the reference arm).
 Multi-GPU: independent replicas, one per rank (nothing is exchanged).
@@ -186,6 +188,58 @@ def oracle_sample(w, solid, modes, budget_s=25.0):
     return per_step, desc, time.perf_counter() - t_start
 
 
+BATCH_CHIS = (32, 48, 64, 40, 56, 32, 64, 48)
+
+
+def batch_configs(precision=1, chis=BATCH_CHIS):
+    """Eight independent 64^3 porous media (sphere packs of radius 5 at 30 %
+    solid, seeds 0-7), chi 32-64, eps 1e-7, smooth seeded starts."""
+    import synth
+    out = []
+    for i, chi in enumerate(chis):
+        out.append(dict(n_per_axis=6, tau=0.7, periodic=(1, 1, 1), solid=synth.sphere_pack(6, 5.0, 0.3, i),
+                        chi_mask=chi, eps_mask=1e-8, force=(1e-5, 0, 0), chi_max=chi, eps=1e-7,
+                        precision=precision, hadamard=0, sweeps=2,
+                        modes=synth.fourier_modes(15, 10 + i, kmax=3, amp_rho=1e-3, amp_u=1e-3),
+                        conserve_mass=precision == 1))
+    return out
+
+
+def batched_measurement(warmup=2, steps=2):
+    """The batched workload: eight simulations stepped in one graph against the
+    same eight stepped one after another, and against one plain FP64
+    full-SVD simulation of the largest chi."""
+    import paper_2512_07615_gb300 as tl
+    N3 = 64 ** 3
+    cfgs = batch_configs()
+    b = tl.Batch(cfgs)
+    info = b.info()
+    b.step(warmup)
+    ms = b.step_timed(steps) / steps
+    b.close()
+    seq = 0.0
+    for c in cfgs:
+        c = dict(c)
+        n = c.pop("n_per_axis")
+        s = tl.Sim(n, **c)
+        s.step(1)
+        seq += s.step_timed(1)
+        s.close()
+    c = dict(batch_configs(precision=0)[2])
+    n = c.pop("n_per_axis")
+    s = tl.Sim(n, **c)
+    s.step(1)
+    ms64 = s.step_timed(1)
+    s.close()
+    return {"workload": "batched8_porous64: eight 64^3 sphere packs (seeds 0-7), chi %s, eps 1e-7, FP32"
+                        % "/".join(map(str, BATCH_CHIS)),
+            "value": len(cfgs) * N3 / (ms * 1e3), "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "launches_per_step": info["launches_per_step"],
+            "jobs_per_step": info["jobs_per_step"],
+            "unbatched_value": len(cfgs) * N3 / (seq * 1e3), "unbatched_ms_per_round": seq,
+            "fp64_unbatched_full_svd_value": N3 / (ms64 * 1e3), "fp64_chi": cfgs[2]["chi_max"]}
+
+
 def cpu_threads():
     try:
         import threadpoolctl
@@ -205,6 +259,7 @@ def main():
     ap.add_argument("--workload", default="porous128", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     N3 = float((1 << w["n"]) ** 3)
@@ -333,6 +388,10 @@ def main():
         cpu = {"value": N3 / sec / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
                "sample": desc, "sample_seconds": round(spent, 1)}
 
+    batched = None
+    if rank == 0 and not args.no_batched and args.workload == "porous128":
+        batched = batched_measurement()
+
     if rank == 0:
         out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -342,7 +401,8 @@ def main():
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
                "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
-               "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu}
+               "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+               "batched": batched}
         print(json.dumps(out))
     sim.close()
     if world > 1:

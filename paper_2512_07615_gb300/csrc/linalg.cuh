@@ -332,47 +332,59 @@ __device__ void householder_qr_par(T* A, int m, int n, int lda, T* Q, int ldq, T
       __syncthreads();
     }
   }
-  // R with non-negative diagonal
+  // R with non-negative diagonal; remember the signs for Q
+  __shared__ signed char s_dneg[1024];
   for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
     const int i = idx / n, c = idx % n;
-    const T d = A[(size_t)i * lda + i] < (T)0 ? (T)-1 : (T)1;
-    R[(size_t)i * ldr + c] = c >= i ? d * A[(size_t)i * lda + c] : (T)0;
-  }
-  // Q = H_0 ... H_{kk-1} [I; 0], backwards
-  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
-    const int i = idx / kk, c = idx % kk;
-    Q[(size_t)i * ldq + c] = (i == c) ? (T)1 : (T)0;
+    const bool neg = A[(size_t)i * lda + i] < (T)0;
+    R[(size_t)i * ldr + c] = c >= i ? (neg ? -A[(size_t)i * lda + c] : A[(size_t)i * lda + c]) : (T)0;
+    if (c == i) s_dneg[i] = neg ? 1 : 0;
   }
   __syncthreads();
+  // Q = H_0 ... H_{kk-1} [I; 0] formed in place of the reflectors, backwards
+  // (column j of A holds reflector j until step j turns it into column j of Q;
+  // columns > j already hold Q, rows < j of them are zero)
   for (int j = kk - 1; j >= 0; --j) {
-    const double tj = tau[j];
-    if (tj == 0.0) continue;
-    const int nc = kk - j;                          // columns j..kk-1
-    for (int base = 0; base < nc * G; base += blockDim.x) {
-      const int t = base + threadIdx.x;
-      const bool act = t < nc * G;
-      const int c = j + t / G, p = t % G;
-      T acc = (T)0;
-      if (act) {
-        if (p == 0) acc = Q[(size_t)j * ldq + c];
-        for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * Q[(size_t)i * ldq + c];
-      }
+    const T tj = (T)tau[j];
+    const int nc = kk - j - 1;                      // Q columns j+1..kk-1
+    if (tj != (T)0 && nc > 0) {
+      for (int base = 0; base < nc * G; base += blockDim.x) {
+        const int t = base + threadIdx.x;
+        const bool act = t < nc * G;
+        const int c = j + 1 + t / G, p = t % G;
+        T acc = (T)0;
+        if (act) {
+          if (p == 0) acc = A[(size_t)j * lda + c];
+          for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
+        }
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
-      if (act && p == 0) wv[c] = acc * (T)tj;
+        for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+        if (act && p == 0) wv[c] = acc * tj;
+      }
+      __syncthreads();
+      const int rows = m - j;
+      for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+        const int ii = j + t / nc, c = j + 1 + t % nc;
+        const T vi = (ii == j) ? (T)1 : A[(size_t)ii * lda + j];
+        A[(size_t)ii * lda + c] -= wv[c] * vi;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const int rows = m - j;
-    for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
-      const int ii = j + t / nc, c = j + t % nc;
-      const T vi = (ii == j) ? (T)1 : A[(size_t)ii * lda + j];
-      Q[(size_t)ii * ldq + c] -= wv[c] * vi;
+    // column j of Q: H_j e_j = e_j - tau_j v, zero above the diagonal
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      T q;
+      if (i < j) q = (T)0;
+      else if (i == j) q = (T)1 - tj;
+      else q = -tj * A[(size_t)i * lda + j];
+      A[(size_t)i * lda + j] = q;
     }
     __syncthreads();
   }
+  // Q out, with the column signs that make diag(R) >= 0
   for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
     const int i = idx / kk, c = idx % kk;
-    if (A[(size_t)c * lda + c] < (T)0) Q[(size_t)i * ldq + c] = -Q[(size_t)i * ldq + c];
+    const T q = A[(size_t)i * lda + c];
+    Q[(size_t)i * ldq + c] = s_dneg[c] ? -q : q;
   }
   __syncthreads();
 }
@@ -446,6 +458,236 @@ __device__ int jacobi_cols_hw(T* Wm, int ldw, T* V, int ldv, int ncol, int len, 
     if (!any) break;
   }
   return sweep;
+}
+
+// 16-byte vector of T
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { typedef float4 t; static constexpr int n = 4; };
+template <> struct Vec16<double> { typedef double2 t; static constexpr int n = 2; };
+
+template <typename T> __device__ __forceinline__ void v_dot3(const typename Vec16<T>::t& x, const typename Vec16<T>::t& y,
+                                                            T& al, T& be, T& ga);
+template <> __device__ __forceinline__ void v_dot3<float>(const float4& x, const float4& y, float& al, float& be, float& ga) {
+  al += x.x * x.x + x.y * x.y + x.z * x.z + x.w * x.w;
+  be += y.x * y.x + y.y * y.y + y.z * y.z + y.w * y.w;
+  ga += x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w;
+}
+template <> __device__ __forceinline__ void v_dot3<double>(const double2& x, const double2& y, double& al, double& be,
+                                                           double& ga) {
+  al += x.x * x.x + x.y * x.y;
+  be += y.x * y.x + y.y * y.y;
+  ga += x.x * y.x + x.y * y.y;
+}
+template <typename T> __device__ __forceinline__ void v_rot(typename Vec16<T>::t& x, typename Vec16<T>::t& y, T c, T s);
+template <> __device__ __forceinline__ void v_rot<float>(float4& x, float4& y, float c, float s) {
+  const float4 a = x, b = y;
+  x = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
+  y = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
+}
+template <> __device__ __forceinline__ void v_rot<double>(double2& x, double2& y, double c, double s) {
+  const double2 a = x, b = y;
+  x = make_double2(c * a.x - s * b.x, c * a.y - s * b.y);
+  y = make_double2(s * a.x + c * b.x, s * a.y + c * b.y);
+}
+
+// One-sided Jacobi (same pair order, tolerance and rotation as jacobi_cols_hw)
+// with a warp per column pair: each column is read once as 16-byte vectors,
+// rotated in registers and written once, so that the shared-memory traffic is
+// one read and one write per column and pair, without bank conflicts.
+// Requires ldw and ldv to be multiples of 16 / sizeof(T) elements, Wm and V
+// 16-byte aligned and len <= 32 * NV * (16 / sizeof(T)).  Column entries
+// [len, round_up(len, 16 / sizeof(T))) are zeroed here, V is set to I.
+template <typename T, int NV>
+__device__ __noinline__ int jacobi_cols_w(T* Wm, int ldw, T* V, int ldv, int ncol, int len, int maxsw) {
+  typedef typename Vec16<T>::t VT;
+  constexpr int VW = Vec16<T>::n;
+  const int lenv = (len + VW - 1) / VW, ncv = (ncol + VW - 1) / VW;
+  const int padw = lenv * VW - len;
+  for (int idx = threadIdx.x; idx < ncol * padw; idx += blockDim.x)
+    Wm[(size_t)(idx / padw) * ldw + len + idx % padw] = (T)0;
+  for (int idx = threadIdx.x; idx < ncol * ncv * VW; idx += blockDim.x) {
+    const int r = idx / (ncv * VW), c = idx % (ncv * VW);
+    V[(size_t)r * ldv + c] = (r == c) ? (T)1 : (T)0;
+  }
+  __shared__ int s_rot;
+  __syncthreads();
+  if (ncol < 2) return 0;
+  const int np = (ncol + 1) & ~1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T tolT = (T)(16.0 * Eps<T>::v * sqrt((double)len));
+  const T floor2 = sizeof(T) == 8 ? (T)1e-250 : (T)1e-24;
+  int sweep = 0;
+  for (; sweep < maxsw; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      for (int p = warp; p < np / 2; p += nw) {
+        int a, b;
+        if (p == 0) { a = rnd; b = np - 1; }
+        else { a = (rnd + p) % (np - 1); b = (rnd - p + (np - 1)) % (np - 1); }
+        if (a > b) { int t = a; a = b; b = t; }
+        if (b >= ncol) continue;                       // the dummy column of an odd count
+        VT* pa = (VT*)(Wm + (size_t)a * ldw);
+        VT* pb = (VT*)(Wm + (size_t)b * ldw);
+        VT xa[NV], xb[NV];
+        T al = (T)0, be = (T)0, ga = (T)0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int i = lane + 32 * v;
+          if (i < lenv) {
+            xa[v] = pa[i];
+            xb[v] = pb[i];
+            v_dot3<T>(xa[v], xb[v], al, be, ga);
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (ga == (T)0 || al < floor2 || be < floor2 || fabs(ga) <= tolT * sqrt(al) * sqrt(be)) continue;
+        const T zeta = (be - al) / ((T)2 * ga);
+        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + hypot((T)1, zeta));
+        const T cc = (T)1 / sqrt((T)1 + t * t), ss = cc * t;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int i = lane + 32 * v;
+          if (i < lenv) {
+            v_rot<T>(xa[v], xb[v], cc, ss);
+            pa[i] = xa[v];
+            pb[i] = xb[v];
+          }
+        }
+        VT* va = (VT*)(V + (size_t)a * ldv);
+        VT* vb = (VT*)(V + (size_t)b * ldv);
+        for (int i = lane; i < ncv; i += 32) {
+          VT x = va[i], y = vb[i];
+          v_rot<T>(x, y, cc, ss);
+          va[i] = x;
+          vb[i] = y;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+// Row stride of a Jacobi matrix for jacobi_cols_fast (16-byte multiple).
+template <typename T>
+__host__ __device__ inline int jacobi_ld(int n) {
+  constexpr int VW = 16 / (int)sizeof(T);
+  return (n + VW - 1) / VW * VW;
+}
+
+// FP32 one-sided Jacobi with a half-warp per column pair (64 pairs in flight
+// in a 1024-thread CTA, as jacobi_cols_hw) and 16-byte vector accesses:
+// each lane holds NV float4 of each of its two columns in registers, so a
+// pair costs one read and one write of each column.  Same pair order,
+// convergence test and rotation as jacobi_cols_hw.  Requires ldw, ldv multiples of 4 and
+// 16-byte aligned Wm, V; len <= 64 * NV.
+template <int NV>
+__device__ __noinline__ int jacobi_cols_h4(float* Wm, int ldw, float* V, int ldv, int ncol, int len, int maxsw) {
+  const int lenv = (len + 3) / 4, ncv = (ncol + 3) / 4;
+  const int padw = lenv * 4 - len;
+  for (int idx = threadIdx.x; idx < ncol * padw; idx += blockDim.x)
+    Wm[(size_t)(idx / padw) * ldw + len + idx % padw] = 0.f;
+  for (int idx = threadIdx.x; idx < ncol * ncv * 4; idx += blockDim.x) {
+    const int r = idx / (ncv * 4), c = idx % (ncv * 4);
+    V[(size_t)r * ldv + c] = (r == c) ? 1.f : 0.f;
+  }
+  __shared__ int s_rot;
+  __syncthreads();
+  if (ncol < 2) return 0;
+  const int np = (ncol + 1) & ~1, nr = np - 1;
+  const int hl = threadIdx.x & 15, hw = threadIdx.x >> 4, nhw = blockDim.x >> 4;
+  const unsigned mask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
+  const float tolT = (float)(16.0 * Eps<float>::v * sqrt((double)len));
+  int sweep = 0;
+  for (; sweep < maxsw; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < nr; ++rnd) {
+      for (int p = hw; p < np / 2; p += nhw) {
+        int a, b;
+        if (p == 0) { a = rnd; b = nr; }
+        else {
+          a = rnd + p; if (a >= nr) a -= nr;
+          b = rnd - p; if (b < 0) b += nr;
+        }
+        if (a > b) { int t = a; a = b; b = t; }
+        const bool live = b < ncol;
+        float4* pa = (float4*)(Wm + (size_t)a * ldw);
+        float4* pb = (float4*)(Wm + (size_t)b * ldw);
+        float4 xa[NV], xb[NV];
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int i = hl + 16 * v;
+          if (live && i < lenv) {
+            xa[v] = pa[i];
+            xb[v] = pb[i];
+            v_dot3<float>(xa[v], xb[v], al, be, ga);
+          }
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(mask, al, o, 16);
+          be += __shfl_xor_sync(mask, be, o, 16);
+          ga += __shfl_xor_sync(mask, ga, o, 16);
+        }
+        if (!live || ga == 0.f || al < 1e-24f || be < 1e-24f || fabsf(ga) <= tolT * sqrtf(al) * sqrtf(be))
+          continue;
+        // Rutishauser's rotation (correctly rounded division and square root:
+        // c^2 + s^2 = 1 to the last bit keeps the accumulated V orthogonal)
+        const float zeta = (be - al) / (2.f * ga);
+        const float az = fabsf(zeta);
+        const float h = az > 1e18f ? az : sqrtf(1.f + zeta * zeta);
+        const float t = copysignf(1.f / (az + h), zeta);
+        const float cc = 1.f / sqrtf(1.f + t * t), ss = cc * t;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int i = hl + 16 * v;
+          if (i < lenv) {
+            v_rot<float>(xa[v], xb[v], cc, ss);
+            pa[i] = xa[v];
+            pb[i] = xb[v];
+          }
+        }
+        float4* va = (float4*)(V + (size_t)a * ldv);
+        float4* vb = (float4*)(V + (size_t)b * ldv);
+        for (int i = hl; i < ncv; i += 16) {
+          float4 x = va[i], y = vb[i];
+          v_rot<float>(x, y, cc, ss);
+          va[i] = x;
+          vb[i] = y;
+        }
+        if (hl == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int any = s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+// The fastest in-CTA Jacobi for the type and column length (use jacobi_ld
+// for the strides): FP32 columns of up to 256 entries take jacobi_cols_h4,
+// everything else jacobi_cols_hw.
+template <typename T>
+__device__ __forceinline__ int jacobi_cols_fast(T* Wm, int ldw, T* V, int ldv, int ncol, int len, int maxsw) {
+  if constexpr (sizeof(T) == 4) {
+    if (len <= 128) return jacobi_cols_h4<2>(Wm, ldw, V, ldv, ncol, len, maxsw);
+    if (len <= 256) return jacobi_cols_h4<4>(Wm, ldw, V, ldv, ncol, len, maxsw);
+  }
+  return jacobi_cols_hw<T>(Wm, ldw, V, ldv, ncol, len, maxsw);
 }
 
 }  // namespace tn

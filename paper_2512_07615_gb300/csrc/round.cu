@@ -12,7 +12,7 @@
 
 namespace tn {
 
-static constexpr int RT = 1024;                     // threads per rounding CTA
+static constexpr int RT = 512;                      // threads per rounding CTA
 static constexpr int SM_SMALL = 44 * 1024;          // bookkeeping part of smem
 static constexpr int SM_WORK = 176 * 1024;          // work area in smem
 static constexpr int MAXK = 1024;                   // max columns of a QR / SVD
@@ -49,9 +49,12 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
     cmax = cm > cmax ? cm : cmax;
     size_t ncol = imin(j.qb[k], (int)(2 * rn));
     size_t len = j.qb[k] > (int)(2 * rn) ? j.qb[k] : 2 * rn;
-    jw = ncol * len > jw ? ncol * len : jw;
-    jv = ncol * ncol > jv ? ncol * ncol : jv;
-    rz = 2 * rn * ncol > rz ? 2 * rn * ncol : rz;     // range-finder power step: n x l
+    // Jacobi matrices with 16-byte row strides (up to 16 / eb - 1 padding)
+    const size_t pad = 16 / eb;
+    jw = ncol * (len + pad) > jw ? ncol * (len + pad) : jw;
+    jv = ncol * (ncol + pad) > jv ? ncol * (ncol + pad) : jv;
+    // range-finder power step (n x l), then B (l x n) of the randomized step
+    rz = (2 * rn + pad) * ncol > rz ? (2 * rn + pad) * ncol : rz;
     size_t u = (size_t)j.qb[k] * imin(j.chi, (int)ncol);
     us = u > us ? u : us;
     // C' = Q_{k-1} (2 q_{k-1} x q_k) * US: 2 q_{k-1} x r
@@ -67,7 +70,6 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   j.lay.us_off = al(us);
   j.lay.rz_off = al(rz);
   j.lay.total = off;
-  (void)eb;
 }
 
 // ---------------------------------------------------------------- device helpers
@@ -171,11 +173,18 @@ static_assert(SM_WV + MAXK * 8 <= SM_SMALL, "bookkeeping overlaps the work area"
 static_assert(16 * 1024 >= (2 * TN_MAXT * (TN_MAXL + 1) + TN_MAXT + 2 * (TN_MAXL + 1) + MAXK) * 4, "bond tables");
 
 // phase timer of thread 0 (profiling only)
+// Phase timers and counters of thread 0, kept in shared memory so that they
+// hold no registers across the kernel (slots: PH_*).
 struct PhaseClock {
   long long t0 = 0;
-  double acc[PH_COUNT] = {0};
+  double* acc;
   bool on;
-  __device__ explicit PhaseClock(bool enable) : on(enable && threadIdx.x == 0) { if (on) t0 = clock64(); }
+  __device__ PhaseClock(bool enable, double* sh) : acc(sh), on(enable && threadIdx.x == 0) {
+    if (on) {
+      for (int p = 0; p < PH_COUNT; ++p) acc[p] = 0.0;
+      t0 = clock64();
+    }
+  }
   __device__ void lap(int ph) {
     if (!on) return;
     const long long t = clock64();
@@ -208,13 +217,15 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
   T* s_wv = (T*)(smem + SM_WV);
   T* work = (T*)(smem + SM_SMALL);
   __shared__ double s_coef[TN_MAXT];
+  __shared__ double s_phase[PH_COUNT];
+  __shared__ double s_flops;                          // algorithmic FLOPs (thread 0)
   __shared__ int s_bad, s_rank;
 
   const int nt = J.nterms;
   T* scr = (T*)J.scratch;
-  double flops = 0.0;                                  // thread 0 only
-  PhaseClock pc(ctr != nullptr);
-  if (threadIdx.x == 0) s_bad = 0;
+  double& flops = s_flops;
+  PhaseClock pc(ctr != nullptr, s_phase);
+  if (threadIdx.x == 0) { s_bad = 0; s_flops = 0.0; }
   __syncthreads();
   // ---- bonds of every term and of the wide sum
   for (int idx = threadIdx.x; idx < nt * (L + 1); idx += blockDim.x) {
@@ -379,10 +390,11 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     // Y (m x l, and n x l in the power steps) must fit the shared work area;
     // B and V (l x n, l x l) go there too when they fit, else to global scratch
     const bool fits = (size_t)imax(m, n) * (lsamp | 1) * sizeof(T) <= (size_t)SM_WORK;
-    const bool bv_smem = ((size_t)lsamp * (n | 1) + (size_t)lsamp * (lsamp | 1)) * sizeof(T) <= (size_t)SM_WORK;
+    const bool bv_smem = ((size_t)lsamp * jacobi_ld<T>(n) + (size_t)lsamp * jacobi_ld<T>(lsamp)) * sizeof(T) <=
+                         (size_t)SM_WORK;
     if (tgt > 0 && lsamp < fullmin && fits && n <= lc->omega_rows && lsamp <= lc->omega_ld) {
       const int l = lsamp;
-      const int ldy = l | 1, ldw = bv_smem ? (n | 1) : n, ldv = bv_smem ? (l | 1) : l;
+      const int ldy = l | 1, ldw = jacobi_ld<T>(n), ldv = jacobi_ld<T>(l);
       T* Ysm = work;
       const T* Om = (const T*)lc->omega;
       // Y = C Omega (m x l), in shared memory
@@ -435,7 +447,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
       for (int idx = threadIdx.x; idx < l * n; idx += blockDim.x)
         Wm[(size_t)(idx / n) * ldw + idx % n] *= (T)scl;
       __syncthreads();
-      const int sw = jacobi_cols_hw<T>(Wm, ldw, Vm, ldv, l, n, 60);
+      const int sw = jacobi_cols_fast<T>(Wm, ldw, Vm, ldv, l, n, 60);
       for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
         T a = (T)0;
         const T* w = Wm + (size_t)jj * ldw;
@@ -503,12 +515,13 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     if (!done) {
       if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
       const bool trans = (n <= m);             // Jacobi on the columns of C
-      const int ldw = len | 1, ldv = ncol | 1;
+      // 16-byte row strides (vector loads in the Jacobi); shared memory if it fits
+      const int ldw = jacobi_ld<T>(len), ldv = jacobi_ld<T>(ncol);
       const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(T);
       T* Wm = (need <= (size_t)SM_WORK) ? work : scr + J.lay.jw_off;
       T* Vm = (need <= (size_t)SM_WORK) ? work + (size_t)ncol * ldw : scr + J.lay.jv_off;
-      const int ldw_e = (need <= (size_t)SM_WORK) ? ldw : len;
-      const int ldv_e = (need <= (size_t)SM_WORK) ? ldv : ncol;
+      const int ldw_e = ldw;
+      const int ldv_e = ldv;
       // scale by an exact power of two so that max |C| is in [1, 2): keeps the
       // Jacobi inner products far from under- and overflow; undone exactly below
       T amax = (T)0;
@@ -533,9 +546,14 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
       __syncthreads();
       const int maxsw = 60;
       pc.lap(PH_SVD_OUT);
-      int sw = jacobi_cols_hw<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
+      const double jac0 = pc.acc[PH_JACOBI];
+      int sw = jacobi_cols_fast<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
       pc.lap(PH_JACOBI);
       if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }   // sweeps, SVD count
+      if (threadIdx.x == 0 && need > (size_t)SM_WORK) {               // matrices in global memory
+        pc.acc[8] += pc.acc[PH_JACOBI] - jac0;
+        pc.acc[9] += 1.0;
+      }
       if (sw >= maxsw && threadIdx.x == 0) {
         flag(status, ST_NOCONV);
         if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big

@@ -409,7 +409,7 @@ class Sim:
         ms = (ctypes.c_double * n)()
         fl = (ctypes.c_double * n)()
         la = (ctypes.c_int * n)()
-        ph = (ctypes.c_double * 8)()
+        ph = (ctypes.c_double * len(nat.ROUND_PHASES))()
         nat.check(nat.lib().tnlbm_profile_step(self.h, ms, fl, la, ph), "tnlbm_profile_step")
         out = {c: dict(ms=ms[i], flops=fl[i], launches=la[i]) for i, c in enumerate(nat.KERNEL_CLASSES)}
         out["round"]["phase_cycles"] = {p: ph[i] for i, p in enumerate(nat.ROUND_PHASES)}
