@@ -20,6 +20,7 @@
 namespace tn {
 
 enum Stage : int { S1 = 0, S2, S3, ENVR, T1, T2, T3, ENVL };
+static constexpr int SPLITK_MAX = 16;     // split-K partials of S3 / T3 held in the X buffer
 
 // Bonds of A, B, C at bond k: from the device arrays (rank) or capacities (bound).
 struct RankSrc {
@@ -103,15 +104,62 @@ __host__ __device__ inline GDesc make_desc(int stage, const FitJob& J, int c, co
   return d;
 }
 
+// Split-K count of one job for the long-K stages: from its capacities only,
+// so that a job does the same arithmetic in any batch.
+__host__ __device__ inline int job_splits(int kcap) {
+  return kcap / 256 < 1 ? 1 : (kcap / 256 > SPLITK_MAX ? SPLITK_MAX : kcap / 256);
+}
+
+// splits > 1 (split-K, for the long-K stages S3 and T3): blockIdx.y = split *
+// nbm + inner batch; each CTA writes the partial product of its K range to the
+// job's X buffer (free during S3 and T3), which fit_splitk_reduce sums in
+// split order (deterministic).
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(G_THREADS) fit_gemm_kernel(const FitJob* __restrict__ jobs, int L,
-                                                             int c, double* ctr) {
+                                                             int c, double* ctr, int splits, int nbm) {
   const FitJob& J = jobs[blockIdx.z];
   RankSrc R{&J, false, L};
   GDesc d = make_desc<T>(STAGE, J, c, R);
   if (ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&ctr[C_FIT_GEMM], 2.0 * d.M * d.N * d.K * d.nb_hi * d.nb_lo);
-  gemm_tile<T>(d, blockIdx.x, blockIdx.y);
+  if (splits <= 1) {
+    gemm_tile<T>(d, blockIdx.x, blockIdx.y, 0, d.K, nullptr);
+    return;
+  }
+  const int split = blockIdx.y / nbm, ib = blockIdx.y % nbm;
+  const int nb = d.nb_hi * d.nb_lo;
+  RankSrc Rc{&J, true, L};
+  const int sj = job_splits(make_desc<T>(STAGE, J, c, Rc).K);
+  if (ib >= nb || split >= sj) return;
+  splits = sj;
+  const int kc = ((d.K + splits - 1) / splits + GB_K - 1) / GB_K * GB_K;
+  const int k0 = imin(d.K, split * kc), k1 = imin(d.K, k0 + kc);
+  T* part = (T*)J.x + ((size_t)split * nb + ib) * d.M * d.N;
+  gemm_tile<T>(d, blockIdx.x, ib, k0, k1, part);
+}
+
+template <typename T, int STAGE>
+__global__ void fit_splitk_reduce(const FitJob* __restrict__ jobs, int L, int c, int splits) {
+  const FitJob& J = jobs[blockIdx.y];
+  RankSrc R{&J, false, L};
+  GDesc d = make_desc<T>(STAGE, J, c, R);
+  RankSrc Rc{&J, true, L};
+  splits = job_splits(make_desc<T>(STAGE, J, c, Rc).K);
+  const int nb = d.nb_hi * d.nb_lo;
+  const size_t mn = (size_t)d.M * d.N, total = mn * nb;
+  const T* part = (const T*)J.x;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int ib = (int)(e / mn);
+    const size_t r = e % mn;
+    const int i = (int)(r / d.N), j = (int)(r % d.N);
+    T acc = (T)0;
+    for (int z = 0; z < splits; ++z) acc += part[((size_t)z * nb + ib) * mn + r];
+    const int hi = ib / d.nb_lo, lo = ib % d.nb_lo;
+    T* p = (T*)d.C + hi * d.c_bh + lo * d.c_bl + i * d.c_rs + j * d.c_cs;
+    T v = (T)d.alpha * acc;
+    if (d.beta != 0.0) v += (T)d.beta * *p;
+    *p = v;
+  }
 }
 
 // ---------------------------------------------------------------- per-job CTA kernels
@@ -244,19 +292,31 @@ static void set_fit_smem() {
 
 // ---------------------------------------------------------------- host driver
 template <typename T, int STAGE>
-static void launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int c,
-                         cudaStream_t st, Prof* prof) {
-  int tiles = 1, nb = 1;
+static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int c,
+                        cudaStream_t st, Prof* prof) {
+  int tiles = 1, nb = 1, kmax = 1;
+  size_t elems = 1;
   for (const FitJob& j : hj) {
     RankSrc R{&j, true, L};
     GDesc d = make_desc<T>(STAGE, j, c, R);
     int t = ((d.M + GB_M - 1) / GB_M) * ((d.N + GB_N - 1) / GB_N);
     tiles = std::max(tiles, t);
     nb = std::max(nb, d.nb_hi * d.nb_lo);
+    kmax = std::max(kmax, d.K);
+    elems = std::max(elems, (size_t)d.M * d.N * d.nb_hi * d.nb_lo);
   }
-  dim3 grid(tiles, nb, (unsigned)hj.size());
-  fit_gemm_kernel<T, STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr);
+  // split-K for the stages whose output tiles alone leave SMs idle (S3, T3:
+  // K = g b); the grid holds the largest per-job split count
+  int splits = 1;
+  if (STAGE == S3 || STAGE == T3) splits = job_splits(kmax);
+  dim3 grid(tiles, nb * splits, (unsigned)hj.size());
+  fit_gemm_kernel<T, STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr, splits, nb);
+  if (splits > 1) {
+    const unsigned rb = (unsigned)std::min<size_t>(64, (elems + 255) / 256);
+    fit_splitk_reduce<T, STAGE><<<dim3(rb, (unsigned)hj.size()), 256, 0, st>>>(d_jobs, L, c, splits);
+  }
   if (prof) prof->mark(C_FIT_GEMM);
+  return splits > 1 ? 2 : 1;
 }
 
 template <typename T>
@@ -272,35 +332,32 @@ int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int swee
   rortho_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, d_status, ctr); ++launches; mark(C_FIT_QR);
   env_edges_kernel<T><<<nj, 32, 0, st>>>(d_jobs, L); ++launches; mark(C_FIT_MISC);
   for (int c = L - 1; c >= 1; --c) {
-    launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
-    launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
-    launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
-    launches += 3;
+    launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
+    launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
+    launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
   }
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int c = 0; c < L; ++c) {
-      launch_stage<T, S1>(d_jobs, hj, L, c, st, prof);
-      launch_stage<T, S2>(d_jobs, hj, L, c, st, prof);
-      launch_stage<T, S3>(d_jobs, hj, L, c, st, prof);
-      launches += 3;
+      launches += launch_stage<T, S1>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, S2>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, S3>(d_jobs, hj, L, c, st, prof);
       if (c < L - 1) {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 0, d_status, ctr); mark(C_FIT_QR);
-        launch_stage<T, ENVR>(d_jobs, hj, L, c, st, prof);
-        launches += 2;
+        launches += launch_stage<T, ENVR>(d_jobs, hj, L, c, st, prof);
+        launches += 1;
       } else {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 2, d_status, ctr); mark(C_FIT_MISC);
         launches += 1;
       }
     }
     for (int c = L - 1; c >= 0; --c) {
-      launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
-      launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
-      launch_stage<T, T3>(d_jobs, hj, L, c, st, prof);
-      launches += 3;
+      launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, T3>(d_jobs, hj, L, c, st, prof);
       if (c > 0) {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 1, d_status, ctr); mark(C_FIT_QR);
-        launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
-        launches += 2;
+        launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
+        launches += 1;
       } else {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 2, d_status, ctr); mark(C_FIT_MISC);
         launches += 1;
@@ -323,6 +380,7 @@ void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* 
     size_t b = bond_cap(L, j.B.cap, c), b1 = bond_cap(L, j.B.cap, c + 1);
     size_t g = bond_cap(L, j.C.cap, c), g1 = bond_cap(L, j.C.cap, c + 1);
     xs = std::max(xs, std::max(a * g * 2 * b1, b * 2 * a1 * g1));
+    xs = std::max(xs, (size_t)SPLITK_MAX * 2 * a * a1);     // split-K partials of S3 and T3
     ys = std::max(ys, std::max(a * 2 * g1 * b1, g * b * 2 * a1));
     ab = std::max(ab, a * 2 * a1);
     q = std::max(q, std::max(a * 2 * a1, std::max(2 * a1 * a, (size_t)2 * a * a)));

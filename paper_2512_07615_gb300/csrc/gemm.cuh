@@ -24,9 +24,13 @@ struct GDesc {
 
 static constexpr int GB_M = 64, GB_N = 64, GB_K = 16, G_THREADS = 256;
 
-// One 64x64 output tile of one inner batch of one descriptor.
+// One 64x64 output tile of one inner batch of one descriptor, over the
+// reduction range [k_begin, k_end).  With part == nullptr the tile is written
+// to C as alpha * AB + beta * C; otherwise the raw sum goes to part (dense
+// M x N, the split-K partial of this range).
 template <typename T>
-__device__ __forceinline__ void gemm_tile(const GDesc& d, int tile, int ib) {
+__device__ __forceinline__ void gemm_tile(const GDesc& d, int tile, int ib, int k_begin, int k_end,
+                                          T* part) {
   __shared__ T As[GB_K][GB_M + 4];
   __shared__ T Bs[GB_K][GB_N + 4];
   const int tn = (d.N + GB_N - 1) / GB_N;
@@ -43,19 +47,19 @@ __device__ __forceinline__ void gemm_tile(const GDesc& d, int tile, int ib) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = (T)0;
-  for (int k0 = 0; k0 < d.K; k0 += GB_K) {
+  for (int k0 = k_begin; k0 < k_end; k0 += GB_K) {
     // A tile: GB_M x GB_K, stored transposed in As[k][m]
     for (int e = threadIdx.x; e < GB_M * GB_K; e += G_THREADS) {
       int mm, kk;
       if (d.a_cs == 1) { mm = e / GB_K; kk = e % GB_K; } else { kk = e / GB_M; mm = e % GB_M; }
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < d.M && gk < d.K) ? A[gm * d.a_rs + gk * d.a_cs] : (T)0;
+      As[kk][mm] = (gm < d.M && gk < k_end) ? A[gm * d.a_rs + gk * d.a_cs] : (T)0;
     }
     for (int e = threadIdx.x; e < GB_K * GB_N; e += G_THREADS) {
       int kk, nn;
       if (d.b_cs == 1) { kk = e / GB_N; nn = e % GB_N; } else { nn = e / GB_K; kk = e % GB_K; }
       const int gk = k0 + kk, gn = n0 + nn;
-      Bs[kk][nn] = (gk < d.K && gn < d.N) ? B[gk * d.b_rs + gn * d.b_cs] : (T)0;
+      Bs[kk][nn] = (gk < k_end && gn < d.N) ? B[gk * d.b_rs + gn * d.b_cs] : (T)0;
     }
     __syncthreads();
 #pragma unroll
@@ -80,6 +84,10 @@ __device__ __forceinline__ void gemm_tile(const GDesc& d, int tile, int ib) {
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx * 4 + j;
       if (gn >= d.N) continue;
+      if (part) {
+        part[(size_t)gm * d.N + gn] = acc[i][j];
+        continue;
+      }
       T* p = C + gm * d.c_rs + gn * d.c_cs;
       T v = (T)d.alpha * acc[i][j];
       if (d.beta != 0.0) v += (T)d.beta * *p;
