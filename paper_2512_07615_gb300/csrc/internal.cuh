@@ -85,7 +85,7 @@ struct Term {
 // Scratch partition of one rounding job (elements of T), same on host and device.
 struct RoundLayout {
   size_t q_off[TN_MAXL + 1];  // left-orthogonal cores of the QR sweep
-  size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, rz_off, total;
+  size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, rz_off, qw_off, total;
 };
 
 // Learned-rank rounding state shared by all jobs of a launch (nullable parts).

@@ -773,3 +773,250 @@ __device__ inline int mlp_predict_rank(const __half* P, const float* spec, float
 }
 
 }  // namespace tn
+
+namespace tn {
+
+// ---------------------------------------------------------------- blocked Householder QR
+// Same factorisation and outputs as householder_qr_par (reflectors, diag(R) >=
+// 0, explicit Q), organised in panels of QB columns (compact WY form,
+// H_p0 ... H_pe-1 = I - V T V^T): the reflectors of a panel are computed column
+// by column on the panel only, and the rest of the matrix is updated once per
+// panel by two small matrix products instead of once per column.  Q is formed
+// backwards panel by panel in place of the reflectors.
+static constexpr int QB = 16;            // panel width
+static constexpr int QNG = 4;            // row groups of the V^T X products
+
+// Scratch (global or shared): vb >= m * QB, wb >= (QNG + 1) * QB * n elements.
+template <typename T>
+__host__ __device__ inline size_t qr_blk_scratch(int m, int n) {
+  return (size_t)m * QB + (size_t)(QNG + 1) * QB * n;
+}
+
+// V (mr x QB, ld QB) of the panel [p0, pe): unit diagonal, zeros above it,
+// the stored reflectors below; columns >= pe - p0 are zero.
+template <typename T>
+__device__ void qr_blk_load_v(const T* A, int lda, int m, int p0, int pe, T* vb) {
+  const int mr = m - p0, pb = pe - p0;
+  for (int idx = threadIdx.x; idx < mr * QB; idx += blockDim.x) {
+    const int r = idx / QB, q = idx % QB;
+    T v;
+    if (q >= pb || r < q) v = (T)0;
+    else if (r == q) v = (T)1;
+    else v = A[(size_t)(p0 + r) * lda + p0 + q];
+    vb[idx] = v;
+  }
+  __syncthreads();
+}
+
+// T (pb x pb, upper) of the compact WY form from the Gram matrix of V:
+// T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] (V^T V)[0:j, j].
+template <typename T>
+__device__ void qr_blk_make_t(const T* vb, int mr, int pb, const double* tau, T (*sT)[QB + 1], T (*sG)[QB + 1]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int pr = warp; pr < pb * pb; pr += nw) {
+    const int q1 = pr / pb, q2 = pr % pb;
+    if (q2 < q1) continue;
+    T acc = (T)0;
+    for (int r = q2 + lane; r < mr; r += 32) acc += vb[(size_t)r * QB + q1] * vb[(size_t)r * QB + q2];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sG[q1][q2] = acc;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int j = 0; j < pb; ++j) {
+      const T tj = (T)tau[j];
+      T z = (T)0;
+      if (lane < j)
+        for (int k = lane; k < j; ++k) z += sT[lane][k] * sG[k][j];
+      __syncwarp();
+      if (lane < j) sT[lane][j] = -tj * z;
+      if (lane == j) sT[j][j] = tj;
+      if (lane > j && lane < QB) sT[lane][j] = (T)0;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// W (pb x nx, ld nx) = V^T X, X = mr x nx (ld ldx): 4x4 register tiles, the
+// rows split over QNG groups whose partials are summed in group order.
+template <typename T>
+__device__ void qr_blk_vtx(const T* vb, int mr, int pb, const T* X, int ldx, int nx, T* wpart, T* W) {
+  const int tq = (pb + 3) >> 2, tc = (nx + 3) >> 2, ntile = tq * tc;
+  const int rc = (mr + QNG - 1) / QNG;
+  for (int it = threadIdx.x; it < ntile * QNG; it += blockDim.x) {
+    const int g = it / ntile, t = it % ntile;
+    const int q0 = (t / tc) * 4, c0 = (t % tc) * 4;
+    const int r0 = g * rc, r1 = imin(mr, r0 + rc);
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int r = r0; r < r1; ++r) {
+      T v[4], x[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v[a] = vb[(size_t)r * QB + q0 + a];     // q0 + 3 < QB
+#pragma unroll
+      for (int b = 0; b < 4; ++b) x[b] = (c0 + b < nx) ? X[(size_t)r * ldx + c0 + b] : (T)0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += v[a] * x[b];
+    }
+    T* wp = wpart + (size_t)g * QB * nx;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      if (q0 + a >= pb) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (c0 + b < nx) wp[(size_t)(q0 + a) * nx + c0 + b] = acc[a][b];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < pb * nx; e += blockDim.x) {
+    T s = (T)0;
+#pragma unroll
+    for (int g = 0; g < QNG; ++g) s += wpart[(size_t)g * QB * nx + e];
+    W[e] = s;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
+                                   double* tau, T* wv, double* red, T* vb, T* wb) {
+  const int kk = imin(m, n);
+  const int G = 8;                                 // threads per column in the panel dots
+  __shared__ T s_scale, s_norm2;
+  __shared__ T sT[QB][QB + 1], sG[QB][QB + 1];
+  __shared__ signed char s_dneg[1024];
+  T* redT = (T*)red;
+  T* wpart = wb;
+  T* W = wb + (size_t)QNG * QB * n;
+  for (int p0 = 0; p0 < kk; p0 += QB) {
+    const int pe = imin(p0 + QB, kk), pb = pe - p0;
+    {                                              // norm of column p0 below its diagonal
+      T part = (T)0;
+      for (int i = p0 + 1 + threadIdx.x; i < m; i += blockDim.x) {
+        const T v = A[(size_t)i * lda + p0];
+        part += v * v;
+      }
+      const T t = block_sum_t<T>(part, redT);
+      if (threadIdx.x == 0) s_norm2 = t;
+    }
+    // ---- panel: column by column, updates restricted to the panel
+    for (int j = p0; j < pe; ++j) {
+      if (threadIdx.x == 0) {
+        const T sig2 = s_norm2;
+        const T alpha = A[(size_t)j * lda + j];
+        if (sig2 == (T)0) {
+          tau[j] = 0.0;
+          s_scale = (T)0;
+        } else {
+          const T beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
+          tau[j] = (double)((beta - alpha) / beta);
+          s_scale = (T)1 / (alpha - beta);
+          A[(size_t)j * lda + j] = beta;
+        }
+      }
+      __syncthreads();
+      const T tj = (T)tau[j];
+      const T sc = s_scale;
+      const int nc = pe - j - 1;
+      if (tj != (T)0 && nc > 0) {
+        for (int base = 0; base < nc * G; base += blockDim.x) {
+          const int t = base + threadIdx.x;
+          const bool act = t < nc * G;
+          const int c = j + 1 + t / G, p = t % G;
+          T acc = (T)0;
+          if (act)
+            for (int i = j + 1 + p; i < m; i += G) acc += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
+#pragma unroll
+          for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, G);
+          if (act && p == 0) wv[c] = (A[(size_t)j * lda + c] + sc * acc) * tj;
+        }
+        __syncthreads();
+      }
+      T part = (T)0;
+      if (tj != (T)0) {
+        const int rows = m - j;
+        if (nc > 0) {
+          for (int t = threadIdx.x; t < rows * nc; t += blockDim.x) {
+            const int ii = j + t / nc, c = j + 1 + t % nc;
+            const T vi = (ii == j) ? (T)1 : sc * A[(size_t)ii * lda + j];
+            const T nv = A[(size_t)ii * lda + c] - wv[c] * vi;
+            A[(size_t)ii * lda + c] = nv;
+            if (c == j + 1 && ii > j + 1) part += nv * nv;
+          }
+        }
+        __syncthreads();
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
+      } else if (nc > 0) {
+        for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) {
+          const T v = A[(size_t)i * lda + j + 1];
+          part += v * v;
+        }
+      }
+      if (j + 1 < pe) {
+        const T t = block_sum_t<T>(part, redT);
+        if (threadIdx.x == 0) s_norm2 = t;
+      } else {
+        __syncthreads();
+      }
+    }
+    // ---- trailing columns [pe, n): A <- (I - V T^T V^T) A
+    const int nt = n - pe, mr = m - p0;
+    if (nt <= 0) continue;
+    qr_blk_load_v<T>(A, lda, m, p0, pe, vb);
+    qr_blk_make_t<T>(vb, mr, pb, tau + p0, sT, sG);
+    T* X = A + (size_t)p0 * lda + pe;
+    qr_blk_vtx<T>(vb, mr, pb, X, lda, nt, wpart, W);
+    for (int e = threadIdx.x; e < pb * nt; e += blockDim.x) {      // W2 = -T^T W (into wpart)
+      const int q = e / nt, c = e % nt;
+      T s = (T)0;
+      for (int q2 = 0; q2 <= q; ++q2) s += sT[q2][q] * W[(size_t)q2 * nt + c];
+      wpart[e] = -s;
+    }
+    __syncthreads();
+    cta_gemm<T>(mr, nt, pb, vb, QB, wpart, nt, X, lda, true);
+  }
+  // ---- R with non-negative diagonal; remember the signs for Q
+  for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
+    const int i = idx / n, c = idx % n;
+    const bool neg = A[(size_t)i * lda + i] < (T)0;
+    R[(size_t)i * ldr + c] = c >= i ? (neg ? -A[(size_t)i * lda + c] : A[(size_t)i * lda + c]) : (T)0;
+    if (c == i) s_dneg[i] = neg ? 1 : 0;
+  }
+  __syncthreads();
+  // ---- Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], backwards, in
+  // place: X = A[p0:m, p0:kk] with the panel's columns reset to unit vectors
+  for (int p0 = ((kk - 1) / QB) * QB; p0 >= 0; p0 -= QB) {
+    const int pe = imin(p0 + QB, kk), pb = pe - p0, mr = m - p0, nx = kk - p0;
+    qr_blk_load_v<T>(A, lda, m, p0, pe, vb);
+    qr_blk_make_t<T>(vb, mr, pb, tau + p0, sT, sG);
+    for (int idx = threadIdx.x; idx < m * pb; idx += blockDim.x) {
+      const int i = idx / pb, c = p0 + idx % pb;
+      A[(size_t)i * lda + c] = (i == c) ? (T)1 : (T)0;
+    }
+    __syncthreads();
+    T* X = A + (size_t)p0 * lda + p0;
+    qr_blk_vtx<T>(vb, mr, pb, X, lda, nx, wpart, W);
+    for (int e = threadIdx.x; e < pb * nx; e += blockDim.x) {      // W2 = -T W (into wpart)
+      const int q = e / nx, c = e % nx;
+      T s = (T)0;
+      for (int q2 = q; q2 < pb; ++q2) s += sT[q][q2] * W[(size_t)q2 * nx + c];
+      wpart[e] = -s;
+    }
+    __syncthreads();
+    cta_gemm<T>(mr, nx, pb, vb, QB, wpart, nx, X, lda, true);
+  }
+  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
+    const int i = idx / kk, c = idx % kk;
+    const T q = A[(size_t)i * lda + c];
+    Q[(size_t)i * ldq + c] = s_dneg[c] ? -q : q;
+  }
+  __syncthreads();
+}
+
+}  // namespace tn

@@ -13,7 +13,7 @@
 namespace tn {
 
 static constexpr int RT = 512;                      // threads per rounding CTA
-static constexpr int SM_SMALL = 44 * 1024;          // bookkeeping part of smem
+static constexpr int SM_SMALL = 41 * 1024;          // bookkeeping part of smem
 static constexpr int SM_WORK = 176 * 1024;          // work area in smem
 static constexpr int MAXK = 1024;                   // max columns of a QR / SVD
 
@@ -33,7 +33,7 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   size_t off = 0;
   auto al = [&](size_t n) { size_t o = off; off += (n + 31) & ~(size_t)31; return o; };
   for (int k = 0; k < L; ++k) j.lay.q_off[k] = al((size_t)2 * j.qb[k] * (k == L - 1 ? 1 : j.qb[k + 1]));
-  size_t wmax = 0, mmax = 0, rmax = 0, cmax = 0, jw = 0, jv = 0, us = 0, rz = 0;
+  size_t wmax = 0, mmax = 0, rmax = 0, cmax = 0, jw = 0, jv = 0, us = 0, rz = 0, qw = 0;
   for (int k = 0; k < L; ++k) {
     size_t w = 0;
     for (int t = 0; t < j.nterms; ++t)
@@ -41,6 +41,9 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
     wmax = w > wmax ? w : wmax;
     size_t m = (size_t)j.qb[k] * 2 * j.rw[k + 1];
     mmax = m > mmax ? m : mmax;
+    // blocked QR of M (2 q_k x rw_{k+1}): panel reflectors and products
+    const size_t qs = qr_blk_scratch<float>(2 * j.qb[k], j.rw[k + 1]);
+    qw = qs > qw ? qs : qw;
     size_t r = (size_t)j.qb[k + 1] * j.rw[k + 1];
     rmax = r > rmax ? r : rmax;
     // right sweep at site k: C is q_k x 2 r_{k+1}, r_{k+1} <= min(chi, q_{k+1})
@@ -69,6 +72,7 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   j.lay.jv_off = al(jv);
   j.lay.us_off = al(us);
   j.lay.rz_off = al(rz);
+  j.lay.qw_off = al(qw);
   j.lay.total = off;
 }
 
@@ -334,7 +338,11 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     // (c) QR of M (mrows x Rk1) -> Q_k (ld rq), new carried R (rq x Rk1, ld Rk1)
     const int rq = imin(mrows, Rk1);
     if (rq > MAXK || Rk1 > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
-    householder_qr_par<T>(M, mrows, Rk1, ld, Qk, rq, Rc, Rk1, s_tau, s_wv, s_red);
+    {
+      T* vb = scr + J.lay.qw_off;
+      householder_qr_blk<T>(M, mrows, Rk1, ld, Qk, rq, Rc, Rk1, s_tau, s_wv, s_red, vb,
+                            vb + (size_t)mrows * QB);
+    }
     if (threadIdx.x == 0) flops += qr_flops(mrows, Rk1);
     pc.lap(PH_QR);
     rc = rq;
