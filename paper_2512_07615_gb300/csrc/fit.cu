@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(FT) rortho_kernel(const FitJob* __restrict__ j
       work[(size_t)i * ldw + c] = Ak[(size_t)c * m + i];
     }
     __syncthreads();
-    householder_qr_par<T>(work, m, n, ldw, Qt, kk, Rm, n, tau, wv, red);
+    householder_qr_blk<T>(work, m, n, ldw, Qt, kk, Rm, n, tau, wv, red, (T*)J.x, (T*)J.x + (size_t)m * QB);
     if (ctr && threadIdx.x == 0) atomicAdd(&ctr[C_FIT_QR], qr_flops(m, n) + 2.0 * 2 * a0 * a * kk);
     // A_k <- Qt^T (kk x m) ; A_{k-1} <- A_{k-1} (2a0 x a) * Rm^T (a x kk)
     for (int idx = threadIdx.x; idx < kk * m; idx += blockDim.x) {
@@ -266,7 +266,9 @@ __global__ void __launch_bounds__(FT) shift_centre_kernel(const FitJob* __restri
     work[(size_t)i * ldw + col] = mode == 0 ? Ab[idx] : Ab[(size_t)col * m + i];
   }
   __syncthreads();
-  householder_qr_par<T>(work, m, n, ldw, Qt, kk, Rm, n, tau, wv, red);
+  // blocked QR; its panel scratch is the X buffer (free between the local update and
+  // the environment update)
+  householder_qr_blk<T>(work, m, n, ldw, Qt, kk, Rm, n, tau, wv, red, (T*)J.x, (T*)J.x + (size_t)m * QB);
   if (ctr && threadIdx.x == 0) atomicAdd(&ctr[C_FIT_QR], qr_flops(m, n));
   if (mode == 0) {
     for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) Ac[idx] = Qt[idx];
@@ -381,6 +383,8 @@ void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* 
     size_t g = bond_cap(L, j.C.cap, c), g1 = bond_cap(L, j.C.cap, c + 1);
     xs = std::max(xs, std::max(a * g * 2 * b1, b * 2 * a1 * g1));
     xs = std::max(xs, (size_t)SPLITK_MAX * 2 * a * a1);     // split-K partials of S3 and T3
+    const size_t amax = std::max(a, a1);
+    xs = std::max(xs, qr_blk_scratch<float>(2 * (int)amax, (int)amax));   // blocked QR panels
     ys = std::max(ys, std::max(a * 2 * g1 * b1, g * b * 2 * a1));
     ab = std::max(ab, a * 2 * a1);
     q = std::max(q, std::max(a * 2 * a1, std::max(2 * a1 * a, (size_t)2 * a * a)));
