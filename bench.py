@@ -43,6 +43,10 @@ WORKLOADS = {
     "porous64": dict(n=6, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
                      chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
                      radius=5.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
+    # Taylor-Green vortex, 256^3, Re = 800 at u0 = 0.05 (nu = u0 (N / 2 pi) / Re)
+    "tgv256": dict(n=8, lattice=19, tau=0.5 + 3.0 * 0.05 * (256 / (2 * 3.141592653589793)) / 800.0,
+                   periodic=(1, 1, 1), force=(0.0, 0.0, 0.0), chi=64, eps=1e-7, chi_mask=1, eps_mask=1e-12,
+                   precision=1, geometry=None, n_modes=0, mode_seed=0, tgv_u0=0.05),
     "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
                       chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
                       n_modes=0, mode_seed=0),
@@ -119,11 +123,13 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(w, solid, modes, budget_s=25.0):
+def oracle_sample(w, solid, modes, budget_s=25.0, pops=None):
     """Time the oracle on the first phases of the same step (moments, rho_0,
     Taylor 1/rho, velocity and second-order products: roundings and fits of
     the real populations) and extrapolate to one whole step by the step's
-    counts of roundings and fits.  Returns (seconds per step, description)."""
+    counts of roundings and fits.  pops: the populations (lists of cores) of
+    the state the GPU timed, else the workload's initial state.  Returns
+    (seconds per step, description, seconds spent)."""
     import oracle.mps as M
     import oracle.mps_lbm as ml
     from oracle import lattice as olat
@@ -152,7 +158,10 @@ def oracle_sample(w, solid, modes, budget_s=25.0):
     # the real populations of the workload (setup, not timed)
     cfg = ml.Config(w["n"], lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=w["chi"],
                     eps=w["eps"], hadamard="fit", mask=None)
-    f = ml.initial_perturbed(cfg, modes) if modes is not None else ml.initial_rest(cfg)
+    if pops is not None:
+        f = [[np.asarray(c, dtype=np.float64) for c in x] for x in pops]
+    else:
+        f = ml.initial_perturbed(cfg, modes) if modes is not None else ml.initial_rest(cfg)
     t_round, t_fit = [], []
     t_start = time.perf_counter()
     # a1: moments
@@ -183,8 +192,8 @@ def oracle_sample(w, solid, modes, budget_s=25.0):
         t_fit.append(time.perf_counter() - t)
     per_step = n_round * float(np.mean(t_round)) + n_fit * float(np.mean(t_fit))
     desc = ("oracle (numpy FP64) on %d roundings and %d fits of the same step (moments tree and "
-            "products of the real populations), extrapolated to the step's %d roundings and %d fits"
-            % (len(t_round), len(t_fit), n_round, n_fit))
+            "products of the %s populations), extrapolated to the step's %d roundings and %d fits"
+            % (len(t_round), len(t_fit), "timed" if pops is not None else "initial", n_round, n_fit))
     return per_step, desc, time.perf_counter() - t_start
 
 
@@ -269,14 +278,19 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     import synth
-    modes = synth.fourier_modes(w["n_modes"], w["mode_seed"], kmax=4, amp_rho=1e-3, amp_u=1e-3) \
-        if w["n_modes"] > 0 else None
+    if w.get("tgv_u0"):
+        modes = synth.taylor_green_modes(w["tgv_u0"])
+    else:
+        modes = synth.fourier_modes(w["n_modes"], w["mode_seed"], kmax=4, amp_rho=1e-3, amp_u=1e-3) \
+            if w["n_modes"] > 0 else None
     solid = geometry(w)
     config = {"workload": args.workload, "lattice": "D3Q%d" % w["lattice"], "cells": "%d^3" % (1 << w["n"]),
               "chi_max": w["chi"], "chi_mask": w["chi_mask"] if solid is not None else None,
               "eps": w["eps"], "tau": w["tau"], "products": "variational fit, 2 sweeps",
               "storage": "fp32" if w["precision"] == 1 else "fp64",
               "mass_correction": w["precision"] == 1,
+              "start": ("Taylor-Green vortex u0 = %g" % w["tgv_u0"]) if w.get("tgv_u0") else
+                       ("%d seeded Fourier modes" % w["n_modes"] if w["n_modes"] else "rest"),
               "l2_flush": "working set > L2 (129 MB) is not claimed; each step touches ~GBs of environments"}
 
     if args.impl == "reference":
@@ -384,7 +398,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sec, desc, spent = oracle_sample(w, solid, modes)
+        sec, desc, spent = oracle_sample(w, solid, modes, pops=sim.get_populations())
         cpu = {"value": N3 / sec / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
                "sample": desc, "sample_seconds": round(spent, 1)}
 

@@ -11,9 +11,9 @@ Every generator takes an explicit seed and uses numpy's PCG64 generator.
 """
 
 from .geometry import channel, sphere_pack, vessel_tree, box_obstacle
-from .fields import fourier_modes, random_mps, feasible_ranks, gaussian_matrix
+from .fields import fourier_modes, random_mps, feasible_ranks, gaussian_matrix, taylor_green_modes
 
 __all__ = [
     "channel", "sphere_pack", "vessel_tree", "box_obstacle",
-    "fourier_modes", "random_mps", "feasible_ranks", "gaussian_matrix",
+    "fourier_modes", "random_mps", "feasible_ranks", "gaussian_matrix", "taylor_green_modes",
 ]

@@ -54,3 +54,28 @@ def feasible_ranks(L, chi):
 def gaussian_matrix(rows, cols, seed):
     """Fixed standard normal test matrix of the randomized range finder."""
     return np.random.default_rng(seed).standard_normal((rows, cols))
+
+
+def taylor_green_modes(u0):
+    """The Taylor-Green vortex in the plane-wave form of fourier_modes, with
+    x = 2 pi X / N:  u = u0 (sin x cos y cos z, -cos x sin y cos z, 0) and the
+    density perturbation 3 u0^2 / 16 (cos 2x + cos 2y)(cos 2z + 2) of its
+    pressure.  Product-to-sum: sin x cos y cos z = 1/4 sum of sin(x +- y +- z),
+    cos x sin y cos z = 1/4 [sin(x+y+z) + sin(x+y-z) - sin(x-y+z) - sin(x-y-z)],
+    and sin t = cos(t - pi/2).  Returns a (10, 8) array (rows as fourier_modes)."""
+    h = -0.5 * np.pi
+    q = u0 / 4.0
+    d = 3.0 * u0 * u0 / 16.0
+    rows = [
+        [1, 1, 1, h, 0.0, q, -q, 0.0],
+        [1, 1, -1, h, 0.0, q, -q, 0.0],
+        [1, -1, 1, h, 0.0, q, q, 0.0],
+        [1, -1, -1, h, 0.0, q, q, 0.0],
+        [2, 0, 2, 0.0, d / 2, 0.0, 0.0, 0.0],
+        [2, 0, -2, 0.0, d / 2, 0.0, 0.0, 0.0],
+        [0, 2, 2, 0.0, d / 2, 0.0, 0.0, 0.0],
+        [0, 2, -2, 0.0, d / 2, 0.0, 0.0, 0.0],
+        [2, 0, 0, 0.0, 2 * d, 0.0, 0.0, 0.0],
+        [0, 2, 0, 0.0, 2 * d, 0.0, 0.0, 0.0],
+    ]
+    return np.array(rows, dtype=np.float64)
