@@ -10,10 +10,10 @@ consume what it returns and do their own arithmetic on it.
 Every generator takes an explicit seed and uses numpy's PCG64 generator.
 """
 
-from .geometry import channel, sphere_pack, vessel_tree, box_obstacle
+from .geometry import channel, sphere_pack, vessel_tree, box_obstacle, sphere_cell, cell_pattern
 from .fields import fourier_modes, random_mps, feasible_ranks, gaussian_matrix, taylor_green_modes
 
 __all__ = [
-    "channel", "sphere_pack", "vessel_tree", "box_obstacle",
+    "channel", "sphere_pack", "vessel_tree", "box_obstacle", "sphere_cell", "cell_pattern",
     "fourier_modes", "random_mps", "feasible_ranks", "gaussian_matrix", "taylor_green_modes",
 ]

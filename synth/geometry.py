@@ -96,3 +96,21 @@ def vessel_tree(n_bits, root_radius, depth, seed, length_factor=3.0,
             child = _unit(np.cos(a) * direction + sign * np.sin(a) * normal)
             stack.append((p1, child, r_child, gen + 1))
     return (~fluid).astype(np.uint8)
+
+
+def sphere_cell(n_bits, radius):
+    """One cell of a periodic array: a solid sphere of `radius` cells centred in
+    a (2^n_bits)^3 cell."""
+    N = 1 << n_bits
+    c = (N - 1) / 2.0
+    x = np.arange(N)
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    return (((X - c) ** 2 + (Y - c) ** 2 + (Z - c) ** 2) <= radius * radius).astype(np.uint8)
+
+
+def cell_pattern(n_bits, fill, seed):
+    """Which cells of a (2^n_bits)^3 arrangement hold the inner geometry: each
+    independently with probability `fill`."""
+    N = 1 << n_bits
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(size=(N, N, N)) < fill).astype(np.uint8)
