@@ -237,6 +237,21 @@ int tnlbm_from_dense(int precision, int n_bits, const void *dense, void *dst,
                      int *dst_ranks, int dst_cap, int chi_max, double eps,
                      void *stream);
 
+/* Mask combined on separate length scales (App. D): an inner geometry on a
+ * (2^n_inner)^3 grid repeated where an outer mask on a (2^n_outer)^3 grid is
+ * one, i.e. m(x) = m_outer(x >> n_inner) m_inner(x mod 2^n_inner) per axis, on
+ * (2^(n_outer + n_inner))^3 cells.  Each part is compressed on its own grid
+ * (TT-SVD as tnlbm_from_dense, chi_max / eps relative to its own norm) and the
+ * outer cores are followed by the inner ones: the largest bond is the larger
+ * of the two, with bond 1 at the junction, and no dense field of the combined
+ * size is formed.  outer_dense / inner_dense: DEVICE [x][y][z] arrays of the
+ * precision's type; dst: DEVICE MPS of L = 3 (n_outer + n_inner) sites and
+ * capacity dst_cap >= chi_max.  Allocates temporaries; synchronous. */
+int tnlbm_mask_product(int precision, int n_outer, const void *outer_dense,
+                       int n_inner, const void *inner_dense, void *dst,
+                       int *dst_ranks, int dst_cap, int chi_max, double eps,
+                       void *stream);
+
 /* ------------------------------------------------------------------ batched simulations
  * Several independent simulations (same n_per_axis, precision and fit sweeps;
  * lattice, geometry, walls, tau, force, chi, eps and start may differ) stepped

@@ -126,6 +126,9 @@ SIGNATURES = {
     "tnlbm_batch_sim": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int]),
     "tnlbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p]),
     "tnlbm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "tnlbm_mask_product": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "tnlbm_materialize": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Term),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.c_int, ctypes.c_void_p]),

@@ -282,6 +282,24 @@ def from_dense(dense, cap, chi_max, eps, stream=None):
     return X
 
 
+def mask_product(outer, inner, cap, chi_max, eps, stream=None):
+    """Combined-scale mask (tnlbm_mask_product): outer and inner are device
+    [x][y][z] tensors of the same float type; returns the DeviceMps of the
+    inner geometry repeated where the outer mask is one."""
+    no = int(outer.shape[0]).bit_length() - 1
+    ni = int(inner.shape[0]).bit_length() - 1
+    p = nat.FP64 if outer.dtype == torch.float64 else nat.FP32
+    if inner.dtype != outer.dtype:
+        raise ValueError("outer and inner must have the same type")
+    X = DeviceMps(3 * (no + ni), cap, p, outer.device)
+    o, i = outer.contiguous(), inner.contiguous()
+    rc = nat.lib().tnlbm_mask_product(p, no, ctypes.c_void_p(o.data_ptr()), ni, ctypes.c_void_p(i.data_ptr()),
+                                      ctypes.c_void_p(X.data.data_ptr()), ctypes.c_void_p(X.ranks.data_ptr()),
+                                      cap, chi_max, eps, _stream(stream))
+    nat.check(rc, "tnlbm_mask_product")
+    return X
+
+
 def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
