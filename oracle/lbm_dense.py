@@ -15,6 +15,8 @@ One step, collide then stream (Eq. evolution):
                    halfway bounce-back value f*_opp(i)(x)  (Eq. boundaries2, no_slip)
   objects          f_i <- (1 - m_O) f_i + S(c_i)(m_O f_opp(i))     (Eq. objects)
                    with the product m_O f_i formed once and used in both terms.
+  faces            optional per-face boundary functions b of Eq. (boundaries2)
+                   instead of bounce-back on every wall face; see face_value.
 
 Fields are arrays f[i, x, y, z].  `mask` is m_O on the grid (binary, or the
 contraction of a mask MPS), or None.
@@ -67,6 +69,60 @@ def boundary_mask(shape, c, periodic):
     return m
 
 
+FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
+
+
+def face_index(d, cd):
+    """Face through which a population with c_d = cd enters: 2d for the plane
+    x_d = 0 (cd > 0), 2d + 1 for x_d = N - 1 (cd < 0)."""
+    return 2 * d + (0 if cd > 0 else 1)
+
+
+def face_masks(shape, c, periodic):
+    """[(face, mask)]: a cell whose upstream neighbour x - c lies outside
+    through several wall faces is assigned to the one of lowest axis; the
+    masks partition the union of the incoming planes."""
+    out = []
+    taken = np.zeros(shape)
+    for d in range(3):
+        cd = int(c[d])
+        if cd == 0 or periodic[d]:
+            continue
+        plane = np.zeros(shape)
+        idx = [slice(None)] * 3
+        idx[d] = 0 if cd > 0 else shape[d] - 1
+        plane[tuple(idx)] = 1.0
+        m = plane * (1.0 - taken)
+        taken = np.maximum(taken, plane)
+        out.append((face_index(d, cd), m))
+    return out
+
+
+def face_value(kind, lat, i, fstar_opp, rho0, u_b, rho_b, P):
+    """Boundary function b(f*_opp(i), rho_b, u_b) of one face (Eqs. no_slip,
+    boundaries2 and the velocity and pressure conditions of Sec. 3.2):
+      wall      f*_opp
+      velocity  f*_opp + 2 w_i rho_0 (c_i . u_b) / c_s^2, c_i pointing into the
+                domain (moving-wall bounce-back, density rho_b = rho_0)
+      pressure  -f*_opp + 2 w_i rho_b (1 + (c_i . u)^2 / (2 c_s^4) - u . u / (2 c_s^2))
+                with u the local fluid velocity, u_d u_e taken as P_de / rho_0
+                (P_de = J~_d u_e of the collision), which makes
+                2 w_i rho_b (1 + sum_{d<=e} kappa_de P_de / rho_0)."""
+    c = lat.c[i].astype(np.float64)
+    w = lat.w[i]
+    if kind == FACE_WALL:
+        return fstar_opp
+    if kind == FACE_VELOCITY:
+        return fstar_opp + 2.0 * w * rho0 * float(c @ np.asarray(u_b, dtype=np.float64)) / CS2
+    if kind == FACE_PRESSURE:
+        acc = np.ones_like(fstar_opp)
+        for de, kap in second_order_coeffs(lat.c[i]).items():
+            if kap != 0.0:
+                acc = acc + kap * P[de] / rho0
+        return -fstar_opp + 2.0 * w * rho_b * acc
+    raise ValueError(kind)
+
+
 def moments(lat, f):
     rho = f.sum(axis=0)
     j = np.einsum("id,i...->d...", lat.c.astype(np.float64), f)
@@ -82,8 +138,11 @@ def second_order_coeffs(c):
     return out
 
 
-def step(f, lat, tau, force=(0.0, 0.0, 0.0), mask=None, periodic=(1, 1, 1), inv_mode="taylor"):
-    """One collide-and-stream step; returns the new populations."""
+def step(f, lat, tau, force=(0.0, 0.0, 0.0), mask=None, periodic=(1, 1, 1), inv_mode="taylor",
+         faces=None):
+    """One collide-and-stream step; returns the new populations.  faces: None
+    (bounce-back on every wall face) or six (kind, u_b, rho_b) for the faces
+    x-, x+, y-, y+, z-, z+ (used on the non-periodic axes)."""
     omega = 1.0 / tau
     F = np.asarray(force, dtype=np.float64)
     m = np.zeros(f.shape[1:]) if mask is None else np.asarray(mask, dtype=np.float64)
@@ -113,9 +172,16 @@ def step(f, lat, tau, force=(0.0, 0.0, 0.0), mask=None, periodic=(1, 1, 1), inv_
                 E += kap * P[de]
         fstar[i] = (1.0 - omega) * f[i] + omega * lat.w[i] * E
     fs = np.empty_like(f)
+    rho0_b = rho.sum() / np.sum(1.0 - m)
     for i in range(lat.Q):
         c = lat.c[i]
-        fs[i] = shift(fstar[i], c, periodic) + boundary_mask(f.shape[1:], c, periodic) * fstar[lat.opp[i]]
+        if faces is None:
+            fs[i] = shift(fstar[i], c, periodic) + boundary_mask(f.shape[1:], c, periodic) * fstar[lat.opp[i]]
+        else:
+            fs[i] = shift(fstar[i], c, periodic)
+            for face, fm in face_masks(f.shape[1:], c, periodic):
+                kind, u_b, rho_b = faces[face]
+                fs[i] = fs[i] + fm * face_value(kind, lat, i, fstar[lat.opp[i]], rho0_b, u_b, rho_b, P)
     if mask is None:
         return fs
     g = m[None] * fs

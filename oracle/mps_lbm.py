@@ -16,7 +16,9 @@ Every population f_i is an MPS on L = 3n binary sites (Sec. 2.4).  One step:
  a7 streaming    f_i <- (x)_d S_d(c_id) f*_i, one axis at a time (x, y, z), each
                  shift an exact MPO (Sec. 2.5) followed by a rounding; on wall axes
                  the non-cyclic shift is used and the last rounding also adds the
-                 halfway bounce-back term m_B,i * f*_opp(i)     (Eq. boundaries2)
+                 halfway bounce-back term m_B,i * f*_opp(i)     (Eq. boundaries2),
+                 or, with per-face boundary functions (cfg.faces), the terms
+                 m_eff * b of boundary_terms
  a8 objects      g_i = f_i * m_O;  f_i <- (f_i - g_i) + S(c_i) g_opp(i)  (Eq. objects),
                  two rounded pairwise sums
  a9 rounding     every sum above is rounded with oracle.mps.round_mps
@@ -46,12 +48,14 @@ import numpy as np
 from . import mps as M
 from .mpo import shift_mpo
 from .quantics import decode
-from .lbm_dense import second_order_coeffs, velocity_out
+from .lbm_dense import (second_order_coeffs, velocity_out, face_index, FACE_WALL, FACE_VELOCITY,
+                        FACE_PRESSURE)
+from .lattice import CS2
 
 
 class Config:
     def __init__(self, n_bits, lattice, tau, force=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
-                 chi_max=16, eps=1e-10, hadamard="fit", sweeps=2, mask=None):
+                 chi_max=16, eps=1e-10, hadamard="fit", sweeps=2, mask=None, faces=None):
         self.n = n_bits
         self.L = 3 * n_bits
         self.N = 1 << n_bits
@@ -64,6 +68,8 @@ class Config:
         self.hadamard = hadamard
         self.sweeps = int(sweeps)
         self.mask = mask                       # MPS cores of m_O or None
+        # None, or six (kind, u_b, rho_b) for the faces x-, x+, y-, y+, z-, z+
+        self.faces = faces
         self.n_fluid = float(self.N ** 3) - (M.inner_ones(mask) if mask is not None else 0.0)
 
 
@@ -118,6 +124,55 @@ def wall_terms(n_bits, c, periodic):
             pv = plane_vectors(n_bits, d, 0 if c[d] > 0 else 1)
             vecs = [(a[0] * b[0], a[1] * b[1]) for a, b in zip(vecs, pv)]
         out.append((coef, vecs))
+    return out
+
+
+def face_terms(n_bits, c, periodic):
+    """[(face, [(sign, vecs)])]: the cells entered through a wall face by
+    velocity c, each assigned to the crossed face of lowest axis (as in
+    oracle.lbm_dense.face_masks), as signed rank-1 plane products
+    m_eff(d) = plane_d prod_{d' < d} (1 - plane_d') expanded."""
+    W = [d for d in range(3) if c[d] != 0 and not periodic[d]]
+    out = []
+    for t, d in enumerate(W):
+        lower = W[:t]
+        terms = []
+        for bits in range(1 << len(lower)):
+            S = [lower[q] for q in range(len(lower)) if bits >> q & 1]
+            vecs = plane_vectors(n_bits, d, 0 if c[d] > 0 else 1)
+            for d2 in S:
+                pv = plane_vectors(n_bits, d2, 0 if c[d2] > 0 else 1)
+                vecs = [(a[0] * b[0], a[1] * b[1]) for a, b in zip(vecs, pv)]
+            terms.append((-1.0 if len(S) % 2 else 1.0, vecs))
+        out.append((face_index(d, c[d]), terms))
+    return out
+
+
+def boundary_terms(cfg, i, fstar_opp, one, rho0, P):
+    """The (coef, MPS) terms m_eff * b of Eq. (boundaries2) for population i
+    with the per-face boundary functions of oracle.lbm_dense.face_value."""
+    lat = cfg.lat
+    c = lat.c[i]
+    w = lat.w[i]
+    out = []
+    for face, terms in face_terms(cfg.n, c, cfg.periodic):
+        kind, u_b, rho_b = cfg.faces[face]
+        for sgn, vecs in terms:
+            if kind == FACE_WALL:
+                out.append((sgn, M.mask_rank1(fstar_opp, vecs)))
+            elif kind == FACE_VELOCITY:
+                out.append((sgn, M.mask_rank1(fstar_opp, vecs)))
+                cu = float(c.astype(np.float64) @ np.asarray(u_b, dtype=np.float64))
+                if cu != 0.0:
+                    out.append((sgn * 2.0 * w * rho0 * cu / CS2, M.mask_rank1(one, vecs)))
+            elif kind == FACE_PRESSURE:
+                out.append((-sgn, M.mask_rank1(fstar_opp, vecs)))
+                out.append((sgn * 2.0 * w * rho_b, M.mask_rank1(one, vecs)))
+                for de, kap in second_order_coeffs(c).items():
+                    if kap != 0.0:
+                        out.append((sgn * 2.0 * w * rho_b * kap / rho0, M.mask_rank1(P[de], vecs)))
+            else:
+                raise ValueError(kind)
     return out
 
 
@@ -267,8 +322,11 @@ def step(cfg, f):
         for t, d in enumerate(axes):
             terms = [(1.0, _shift(cfg, x, d, c[d]))]
             if t == len(axes) - 1:
-                for coef, vecs in walls:
-                    terms.append((coef, M.mask_rank1(fstar[lat.opp[i]], vecs)))
+                if cfg.faces is None:
+                    for coef, vecs in walls:
+                        terms.append((coef, M.mask_rank1(fstar[lat.opp[i]], vecs)))
+                else:
+                    terms += boundary_terms(cfg, i, fstar[lat.opp[i]], one, rho0, P)
             x = _R(cfg, terms)
         fs.append(x)
     if cfg.mask is None:
