@@ -92,7 +92,25 @@ typedef struct {
                               at the start): removes the ~1e-6-per-step mass
                               drift of FP32 core storage.  Not part of the
                               paper's method; default 0                         */
+  /* Boundary function of each face on the non-periodic axes (Eq. boundaries2),
+   * faces ordered x-, x+, y-, y+, z-, z+ (x- = the plane x = 0):
+   *   TNLBM_FACE_WALL      halfway bounce-back (Eq. no_slip), the default
+   *   TNLBM_FACE_VELOCITY  inlet at velocity face_u: f_i = f*_opp(i) +
+   *                        2 w_i rho_0 (c_i . u_b) / c_s^2, c_i pointing into
+   *                        the domain (moving-wall bounce-back, rho_b = rho_0);
+   *                        tnlbm_set_face_velocity changes u_b between steps
+   *   TNLBM_FACE_PRESSURE  outlet at density face_rho: f_i = -f*_opp(i) +
+   *                        2 w_i rho_b (1 + (c_i.u)^2 / (2 c_s^4) - u.u / (2 c_s^2))
+   *                        with the local velocity, u_d u_e = P_de / rho_0
+   * A cell entered through several wall faces takes the face of lowest axis.
+   * All faces TNLBM_FACE_WALL reproduces the plain bounce-back step.  Faces on
+   * periodic axes must stay TNLBM_FACE_WALL (they are not used). */
+  int face_kind[6];
+  double face_u[6][3];
+  double face_rho[6];
 } tnlbm_config;
+
+enum { TNLBM_FACE_WALL = 0, TNLBM_FACE_VELOCITY = 1, TNLBM_FACE_PRESSURE = 2 };
 
 typedef struct {
   int64_t steps;             /* steps taken so far                               */
@@ -125,6 +143,10 @@ int tnlbm_get_populations(tnlbm_sim *s, double *cores, int *ranks);
 int tnlbm_set_populations(tnlbm_sim *s, const double *cores, const int *ranks);
 
 int tnlbm_stats_get(tnlbm_sim *s, tnlbm_stats *out);
+
+/* Inlet velocity u_b of a TNLBM_FACE_VELOCITY face (0..5) from the next step
+ * on (a time-dependent inflow sets it before every step); synchronous. */
+int tnlbm_set_face_velocity(tnlbm_sim *s, int face, const double *u);
 
 /* Advance k steps through the captured graph and return the device time of
  * the k launches in *ms (CUDA events on the simulation's stream). */

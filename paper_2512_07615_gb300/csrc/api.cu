@@ -352,6 +352,22 @@ struct Builder {
       fstar[i] = R({P(S.f_state[i], 1.0 - omega), P(Y, omega * lat.w[i])});
     }
     // a7 streaming
+    bool use_faces = false;
+    for (int f6 = 0; f6 < 6; ++f6) use_faces = use_faces || S.cfg.face_kind[f6] != TNLBM_FACE_WALL;
+    int ones_node = -1;
+    if (use_faces) {
+      // the all-ones MPS (rank 1), operand of the masked constant terms
+      ones_node = new_node(s, 1, 0);
+      if (ones_node < 0) { oom = true; return; }
+      const size_t ne = mps_size(S.L, 1);
+      if (S.prec == TNLBM_FP64) {
+        std::vector<double> h(ne, 1.0);
+        cudaMemcpy(S.nodes[ones_node].base, h.data(), ne * sizeof(double), cudaMemcpyHostToDevice);
+      } else {
+        std::vector<float> h(ne, 1.0f);
+        cudaMemcpy(S.nodes[ones_node].base, h.data(), ne * sizeof(float), cudaMemcpyHostToDevice);
+      }
+    }
     std::vector<int> fs(Q);
     for (int i = 0; i < Q; ++i) {
       const int* c = lat.c[i];
@@ -362,7 +378,7 @@ struct Builder {
       for (int d : axes) if (!S.cfg.periodic[d]) W.push_back(d);
       for (size_t t = 0; t < axes.size(); ++t) {
         std::vector<TermSpec> ts = {SH(x, axes[t], c[axes[t]])};
-        if (t + 1 == axes.size()) {
+        if (t + 1 == axes.size() && !use_faces) {
           for (int bits = 1; bits < (1 << W.size()); ++bits) {
             std::vector<int> sub;
             for (size_t q = 0; q < W.size(); ++q) if (bits >> q & 1) sub.push_back(W[q]);
@@ -370,6 +386,43 @@ struct Builder {
             m.coef = (sub.size() % 2 == 1) ? 1.0 : -1.0;
             m.mask_id = mask_plane_product(sub, c);
             ts.push_back(m);
+          }
+        } else if (t + 1 == axes.size()) {
+          // per-face boundary functions: the cells entered through wall axis
+          // W[wi] and none of lower index, plane_d prod (1 - plane_d') expanded
+          const double wi_ = lat.w[i];
+          for (size_t wi = 0; wi < W.size(); ++wi) {
+            const int d = W[wi];
+            const int face = 2 * d + (c[d] > 0 ? 0 : 1);
+            const int kind = S.cfg.face_kind[face];
+            for (int bits = 0; bits < (1 << wi); ++bits) {
+              std::vector<int> axset = {d};
+              int cnt = 0;
+              for (size_t q = 0; q < wi; ++q)
+                if (bits >> q & 1) { axset.push_back(W[q]); ++cnt; }
+              const double sgn = (cnt % 2) ? -1.0 : 1.0;
+              const int mid = mask_plane_product(axset, c);
+              auto MK = [&](int node, double coef, int slot) {
+                TermSpec m; m.kind = T_MASK1; m.x = node; m.coef = coef; m.coef_slot = slot; m.mask_id = mid;
+                return m;
+              };
+              if (kind == TNLBM_FACE_WALL) {
+                ts.push_back(MK(fstar[lat.opp[i]], sgn, -1));
+              } else if (kind == TNLBM_FACE_VELOCITY) {
+                ts.push_back(MK(fstar[lat.opp[i]], sgn, -1));
+                for (int e = 0; e < 3; ++e)          // 2 w_i c_ie (rho_0 u_b,e) / c_s^2
+                  if (c[e] != 0) ts.push_back(MK(ones_node, sgn * 6.0 * wi_ * c[e], SC_UB + 3 * face + e));
+              } else {
+                const double rb = S.cfg.face_rho[face];
+                ts.push_back(MK(fstar[lat.opp[i]], -sgn, -1));
+                ts.push_back(MK(ones_node, sgn * 2.0 * wi_ * rb, -1));
+                for (int d1 = 0; d1 < 3; ++d1)
+                  for (int e1 = d1; e1 < 3; ++e1) {
+                    const double kap = d1 == e1 ? 4.5 * c[d1] * c[d1] - 1.5 : 9.0 * c[d1] * c[e1];
+                    if (kap != 0.0) ts.push_back(MK(Pm[d1][e1], sgn * 2.0 * wi_ * rb * kap, SC_INV1));
+                  }
+              }
+            }
           }
         }
         x = R(ts);
@@ -678,6 +731,13 @@ static int create_impl(tnlbm_sim* s) {
   s->d_status = (int*)s->arena.alloc(STATUS_INTS * sizeof(int));
   if (!s->d_scal || !s->d_status) return TNLBM_E_OOM;
   cudaMemset(s->d_scal, 0, SC_COUNT * sizeof(double));
+  {
+    double ub[18] = {0};                     // inlet velocities of the velocity faces
+    for (int f6 = 0; f6 < 6; ++f6)
+      if (C.face_kind[f6] == TNLBM_FACE_VELOCITY)
+        for (int d = 0; d < 3; ++d) ub[3 * f6 + d] = C.face_u[f6][d];
+    cudaMemcpy(s->d_scal + SC_UBRAW, ub, sizeof(ub), cudaMemcpyHostToDevice);
+  }
   cudaMemset(s->d_status, 0, STATUS_INTS * sizeof(int));
   const int Q = s->lat.Q;
   // state
@@ -837,6 +897,15 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (C.mask_cores && (!C.mask_ranks || C.mask_cap < 1)) { set_error("mask_ranks / mask_cap missing"); return TNLBM_E_ARG; }
   if (C.solid && (C.chi_mask < 1 || C.chi_mask > 512)) { set_error("chi_mask must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.n_modes < 0 || (C.n_modes > 0 && !C.modes)) { set_error("modes missing"); return TNLBM_E_ARG; }
+  for (int f6 = 0; f6 < 6; ++f6) {
+    const int k = C.face_kind[f6];
+    if (k < TNLBM_FACE_WALL || k > TNLBM_FACE_PRESSURE) { set_error("bad face_kind"); return TNLBM_E_ARG; }
+    if (k != TNLBM_FACE_WALL && C.periodic[f6 / 2]) {
+      set_error("inlet / outlet faces need a non-periodic axis");
+      return TNLBM_E_ARG;
+    }
+    if (k == TNLBM_FACE_PRESSURE && !(C.face_rho[f6] > 0.0)) { set_error("face_rho must be > 0"); return TNLBM_E_ARG; }
+  }
   tnlbm_sim* s = new (std::nothrow) tnlbm_sim();
   if (!s) { set_error("host allocation failed"); return TNLBM_E_OOM; }
   s->n = C.n_per_axis;
@@ -1045,6 +1114,18 @@ int tnlbm_learn_counters(tnlbm_sim* s, long long* out, int reset) {
   TN_CUDA(cudaMemcpy(hc, s->d_lcount, sizeof(hc), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 3; ++i) out[i] = hc[i];
   if (reset) TN_CUDA(cudaMemset(s->d_lcount, 0, 3 * sizeof(int)));
+  return 0;
+}
+
+int tnlbm_set_face_velocity(tnlbm_sim* s, int face, const double* u) {
+  if (!s || face < 0 || face > 5 || !u) { set_error("bad arguments to tnlbm_set_face_velocity"); return TNLBM_E_ARG; }
+  if (s->cfg.face_kind[face] != TNLBM_FACE_VELOCITY) {
+    set_error("tnlbm_set_face_velocity: the face is not a velocity face");
+    return TNLBM_E_ARG;
+  }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  TN_CUDA(cudaMemcpy(s->d_scal + SC_UBRAW + 3 * face, u, 3 * sizeof(double), cudaMemcpyHostToDevice));
+  for (int d = 0; d < 3; ++d) s->cfg.face_u[face][d] = u[d];
   return 0;
 }
 

@@ -64,7 +64,11 @@ template <typename T>
 void launch_inner_ones(const MpsRef* d_refs, int n, int L, double* d_out, cudaStream_t st);
 
 // rho_0 = <rho,1> / n_fluid and the scalar slots used by the Taylor 1/rho terms
-enum ScalSlot : int { SC_NEG_RHO0 = 0, SC_INV1 = 1, SC_INV2 = 2, SC_INV3 = 3, SC_RHO0 = 4, SC_COUNT = 8 };
+// scalars of a step: rho_0 and its powers (Sec. 3.2), and per face (x-, x+, y-,
+// y+, z-, z+) the inlet velocity u_b as set by the host (SC_UBRAW + 3 face + d)
+// and rho_0 u_b (SC_UB + 3 face + d), the coefficient scale of Eq. boundaries2
+enum ScalSlot : int { SC_NEG_RHO0 = 0, SC_INV1 = 1, SC_INV2 = 2, SC_INV3 = 3, SC_RHO0 = 4, SC_UB = 8,
+                      SC_UBRAW = 26, SC_COUNT = 44 };
 template <typename T>
 void launch_rho0(const MpsRef* d_rho, int L, double n_fluid, double* d_scal, cudaStream_t st);
 

@@ -59,6 +59,7 @@ __global__ void rho0_kernel(const MpsRef* rho, int L, double n_fluid, double* sc
     scal[SC_INV2] = -1.0 / (r0 * r0);
     scal[SC_INV3] = 1.0 / (r0 * r0 * r0);
     scal[SC_RHO0] = r0;
+    for (int q = 0; q < 18; ++q) scal[SC_UB + q] = r0 * scal[SC_UBRAW + q];
   }
 }
 

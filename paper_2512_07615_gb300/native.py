@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "libtnlbm.so")
 
 FP64, FP32 = 0, 1
 D3Q19, D3Q15 = 19, 15
+FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
 HADAMARD_FIT, HADAMARD_EXACT = 0, 1
 TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy")
@@ -42,6 +43,9 @@ class Config(ctypes.Structure):
         ("modes", c_double_p),
         ("max_jobs_in_flight", ctypes.c_int),
         ("conserve_mass", ctypes.c_int),
+        ("face_kind", ctypes.c_int * 6),
+        ("face_u", (ctypes.c_double * 3) * 6),
+        ("face_rho", ctypes.c_double * 6),
     ]
 
 
@@ -129,6 +133,7 @@ SIGNATURES = {
     "tnlbm_mask_product": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
+    "tnlbm_set_face_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
     "tnlbm_materialize": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Term),
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                          ctypes.c_int, ctypes.c_void_p]),

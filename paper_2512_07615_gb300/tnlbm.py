@@ -303,9 +303,11 @@ def mask_product(outer, inner, cap, chi_max, eps, stream=None):
 def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
-                conserve_mass=False):
+                conserve_mass=False, faces=None):
     """tnlbm_config for the arguments; returns (config, arrays the config
-    points to, which must stay alive until the simulation is created)."""
+    points to, which must stay alive until the simulation is created).
+    faces: None (bounce-back on every wall face) or a dict face -> (kind, u_b,
+    rho_b), faces 0..5 = x-, x+, y-, y+, z-, z+, kind nat.FACE_*."""
     c = nat.Config()
     c.n_per_axis = n_per_axis
     c.lattice = lattice
@@ -339,6 +341,11 @@ def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), soli
     c.hadamard = hadamard
     c.sweeps = sweeps
     c.conserve_mass = int(bool(conserve_mass))
+    for f6, (kind, u_b, rho_b) in (faces or {}).items():
+        c.face_kind[f6] = int(kind)
+        for d in range(3):
+            c.face_u[f6][d] = float(u_b[d])
+        c.face_rho[f6] = float(rho_b)
     if modes is not None:
         m = np.ascontiguousarray(modes, dtype=np.float64)
         keep.append(m)
@@ -466,6 +473,11 @@ class Sim:
         out = (ctypes.c_longlong * 3)()
         nat.check(nat.lib().tnlbm_learn_counters(self.h, out, int(reset)), "tnlbm_learn_counters")
         return tuple(out)
+
+    def set_face_velocity(self, face, u):
+        """Inlet velocity of a velocity face from the next step on."""
+        arr = (ctypes.c_double * 3)(*[float(x) for x in u])
+        nat.check(nat.lib().tnlbm_set_face_velocity(self.h, face, arr), "tnlbm_set_face_velocity")
 
     def stats(self):
         s = nat.Stats()
