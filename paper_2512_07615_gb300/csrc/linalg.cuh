@@ -883,6 +883,24 @@ __device__ void qr_blk_vtx(const T* vb, int mr, int pb, const T* X, int ldx, int
   __syncthreads();
 }
 
+// Squared-norm floor of the Householder columns: m (4 eps max|A|)^2, the
+// rounding noise of the matrix in its own type.
+template <typename T>
+__device__ T qr_noise_floor2(const T* A, int m, int n, int lda, T* red) {
+  T amax = (T)0;
+  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x)
+    amax = fmax(amax, fabs(A[(size_t)(idx / n) * lda + idx % n]));
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  T a = (T)0;
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) a = fmax(a, red[w]);
+  __syncthreads();
+  const T f = (T)(4.0 * Eps<T>::v) * a;
+  return (T)m * f * f;
+}
+
 template <typename T>
 __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
                                    double* tau, T* wv, double* red, T* vb, T* wb) {
@@ -894,6 +912,10 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
   T* redT = (T*)red;
   T* wpart = wb;
   T* W = wb + (size_t)QNG * QB * n;
+  // columns below the rounding floor of the matrix are zero: a reflector built
+  // from them (with squares near the underflow range) is not orthogonal and
+  // would spoil the larger columns it is applied to
+  const T floor2 = qr_noise_floor2<T>(A, m, n, lda, redT);
   for (int p0 = 0; p0 < kk; p0 += QB) {
     const int pe = imin(p0 + QB, kk), pb = pe - p0;
     {                                              // norm of column p0 below its diagonal
@@ -910,9 +932,9 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
       if (threadIdx.x == 0) {
         const T sig2 = s_norm2;
         const T alpha = A[(size_t)j * lda + j];
-        if (sig2 == (T)0) {
+        if (sig2 <= floor2) {
           tau[j] = 0.0;
-          s_scale = (T)0;
+          s_scale = sig2 == (T)0 ? (T)0 : (T)-1;    // -1: zero the column below the diagonal
         } else {
           const T beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
           tau[j] = (double)((beta - alpha) / beta);
@@ -923,6 +945,8 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
       __syncthreads();
       const T tj = (T)tau[j];
       const T sc = s_scale;
+      if (tj == (T)0 && sc == (T)-1)
+        for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] = (T)0;
       const int nc = pe - j - 1;
       if (tj != (T)0 && nc > 0) {
         for (int base = 0; base < nc * G; base += blockDim.x) {

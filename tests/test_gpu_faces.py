@@ -3,7 +3,7 @@ step with per-face boundary functions equals the dense step untruncated
 (FP64, exact products; mixed faces with shared edges); an inlet velocity
 changed between steps follows the same sequence in the dense step; a uniform
 stream at the inlet velocity and outlet density stays put; and the FP32
-production path of an inlet-filled box tracks the dense oracle."""
+production path of an inlet / outlet channel tracks the dense oracle."""
 import numpy as np
 import pytest
 
@@ -80,14 +80,12 @@ def test_uniform_stream_stays_put(tl):
     sim.close()
 
 
-def test_inlet_fp32_tracks_dense(tl):
-    """32^3 box along x filled through an inlet of 0.04 at x = 0 (walls at
-    x = N-1 and z, periodic y); FP32, variational products, chi 32, 10 steps.
-    (With a pressure outlet the FP32 path needs eps >= 1e-5: at eps below the
-    FP32 resolution its roundings keep rounding noise up to chi, and the error
-    of the outlet rows grows to 1e-3 of the density; the FP64 path is exact.)"""
+def test_inlet_outlet_fp32_tracks_dense(tl):
+    """32^3 channel along x: inlet 0.04 at x = 0, outlet density 1 at x = N-1,
+    walls at z (periodic y); FP32, variational products, chi 32, eps 1e-7,
+    10 steps, against the dense oracle."""
     n, tau = 5, 0.8
-    spec = {0: (V, (0.04, 0.0, 0.0), 1.0)}
+    spec = {0: (V, (0.04, 0.0, 0.0), 1.0), 1: (P, (0.0, 0.0, 0.0), 1.0)}
     sim = tl.Sim(n, tau=tau, periodic=(0, 1, 0), chi_max=32, eps=1e-7, precision=1, hadamard=0, faces=spec)
     sim.step(10)
     rho, u = sim.macroscopic()
