@@ -55,7 +55,8 @@ from .lattice import CS2
 
 class Config:
     def __init__(self, n_bits, lattice, tau, force=(0.0, 0.0, 0.0), periodic=(1, 1, 1),
-                 chi_max=16, eps=1e-10, hadamard="fit", sweeps=2, mask=None, faces=None):
+                 chi_max=16, eps=1e-10, hadamard="fit", sweeps=2, mask=None, faces=None,
+                 block_sums=False):
         self.n = n_bits
         self.L = 3 * n_bits
         self.N = 1 << n_bits
@@ -70,6 +71,9 @@ class Config:
         self.mask = mask                       # MPS cores of m_O or None
         # None, or six (kind, u_b, rho_b) for the faces x-, x+, y-, y+, z-, z+
         self.faces = faces
+        # moments as one rounded block sum of all populations instead of the
+        # pairwise tree (the alternative linear fold)
+        self.block_sums = bool(block_sums)
         self.n_fluid = float(self.N ** 3) - (M.inner_ones(mask) if mask is not None else 0.0)
 
 
@@ -87,8 +91,12 @@ def _had(cfg, B, C):
 
 def tree_sum(cfg, items):
     """Balanced pairwise reduction of [(coef, MPS), ...]; each pair is one
-    rounded two-term sum, an odd last item moves up unchanged."""
+    rounded two-term sum, an odd last item moves up unchanged.  With
+    cfg.block_sums: one rounding of the whole block sum (Eq. add over all
+    terms, then the rounding sweep once)."""
     items = list(items)
+    if cfg.block_sums and len(items) > 1:
+        return _R(cfg, items)
     while len(items) > 1:
         nxt = []
         for p in range(0, len(items) - 1, 2):

@@ -61,3 +61,4 @@ def test_mps_faces_equal_dense_untruncated():
                  "taylor")
     assert np.abs(fw - ld.step(ml.to_dense_populations(ml.initial_perturbed(cfg, modes)), lat, 0.8, (0, 0, 0),
                                None, (0, 1, 0), "taylor", faces=faces)).max() > 1e-4
+
