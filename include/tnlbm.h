@@ -108,6 +108,9 @@ typedef struct {
   int face_kind[6];
   double face_u[6][3];
   double face_rho[6];
+  int block_sums;          /* 1: the moments as one rounding of the block sum of
+                              all Q populations (Eq. add over all terms) instead
+                              of the pairwise tree; needs Q chi_max <= 1024     */
 } tnlbm_config;
 
 enum { TNLBM_FACE_WALL = 0, TNLBM_FACE_VELOCITY = 1, TNLBM_FACE_PRESSURE = 2 };

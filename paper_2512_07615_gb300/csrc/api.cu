@@ -247,6 +247,7 @@ struct Builder {
   }
 
   int tree_sum(std::vector<TermSpec> items) {
+    if (s->cfg.block_sums && items.size() > 1) return R(items);   // one rounding of the block sum
     while (items.size() > 1) {
       std::vector<TermSpec> nxt;
       for (size_t p = 0; p + 1 < items.size(); p += 2) nxt.push_back(P(R({items[p], items[p + 1]}), 1.0));
@@ -897,6 +898,10 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (C.mask_cores && (!C.mask_ranks || C.mask_cap < 1)) { set_error("mask_ranks / mask_cap missing"); return TNLBM_E_ARG; }
   if (C.solid && (C.chi_mask < 1 || C.chi_mask > 512)) { set_error("chi_mask must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.n_modes < 0 || (C.n_modes > 0 && !C.modes)) { set_error("modes missing"); return TNLBM_E_ARG; }
+  if (C.block_sums && (C.lattice * C.chi_max > 1024)) {
+    set_error("block_sums needs Q * chi_max <= 1024 (the summed bond of one rounding)");
+    return TNLBM_E_ARG;
+  }
   for (int f6 = 0; f6 < 6; ++f6) {
     const int k = C.face_kind[f6];
     if (k < TNLBM_FACE_WALL || k > TNLBM_FACE_PRESSURE) { set_error("bad face_kind"); return TNLBM_E_ARG; }

@@ -46,6 +46,7 @@ class Config(ctypes.Structure):
         ("face_kind", ctypes.c_int * 6),
         ("face_u", (ctypes.c_double * 3) * 6),
         ("face_rho", ctypes.c_double * 6),
+        ("block_sums", ctypes.c_int),
     ]
 
 

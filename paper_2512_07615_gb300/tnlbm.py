@@ -303,7 +303,7 @@ def mask_product(outer, inner, cap, chi_max, eps, stream=None):
 def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
-                conserve_mass=False, faces=None):
+                conserve_mass=False, faces=None, block_sums=False):
     """tnlbm_config for the arguments; returns (config, arrays the config
     points to, which must stay alive until the simulation is created).
     faces: None (bounce-back on every wall face) or a dict face -> (kind, u_b,
@@ -341,6 +341,7 @@ def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), soli
     c.hadamard = hadamard
     c.sweeps = sweeps
     c.conserve_mass = int(bool(conserve_mass))
+    c.block_sums = int(bool(block_sums))
     for f6, (kind, u_b, rho_b) in (faces or {}).items():
         c.face_kind[f6] = int(kind)
         for d in range(3):
