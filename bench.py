@@ -47,6 +47,12 @@ WORKLOADS = {
     "tgv256": dict(n=8, lattice=19, tau=0.5 + 3.0 * 0.05 * (256 / (2 * 3.141592653589793)) / 800.0,
                    periodic=(1, 1, 1), force=(0.0, 0.0, 0.0), chi=64, eps=1e-7, chi_mask=1, eps_mask=1e-12,
                    precision=1, geometry=None, n_modes=0, mode_seed=0, tgv_u0=0.05),
+    # branching vessel, 256^3: binary tree of cylinders (depth 4, Murray radii
+    # from 24 cells, bifurcation half-angles 25-45 deg), body force along the
+    # root axis in the fluid; FP32 storage and contractions (no BF16 path)
+    "vessel256": dict(n=8, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
+                      chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=1, geometry="vessel",
+                      radius=24.0, depth=4, geo_seed=0, n_modes=31, mode_seed=0),
     "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
                       chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
                       n_modes=0, mode_seed=0),
@@ -62,6 +68,8 @@ def geometry(w):
     import synth
     if w["geometry"] == "spheres":
         return synth.sphere_pack(w["n"], w["radius"], w["solid_fraction"], w["geo_seed"])
+    if w["geometry"] == "vessel":
+        return synth.vessel_tree(w["n"], w["radius"], w["depth"], w["geo_seed"])
     return None
 
 
@@ -249,6 +257,56 @@ def batched_measurement(warmup=2, steps=2):
             "fp64_unbatched_full_svd_value": N3 / (ms64 * 1e3), "fp64_chi": cfgs[2]["chi_max"]}
 
 
+MIXED_SIZES = (6, 7, 8, 6, 7, 6, 8, 7)
+MIXED_CHIS = (32, 64, 128)
+
+
+def mixed_batch_configs():
+    """Eight simulations of uneven size: 64^3 / 128^3 / 256^3 in the order of
+    MIXED_SIZES, chi cycling 32 / 64 / 128; even seeds are sphere packs (radius
+    10 cells per 128, 35 % solid), odd seeds branching vessels (root radius 24
+    cells per 256, depth 4); FP32, eps 1e-7, seeded smooth starts."""
+    import synth
+    out = []
+    for i, n in enumerate(MIXED_SIZES):
+        N = 1 << n
+        chi = MIXED_CHIS[i % 3]
+        solid = synth.sphere_pack(n, 10.0 * N / 128, 0.35, i) if i % 2 == 0 else \
+            synth.vessel_tree(n, 24.0 * N / 256, 4, i)
+        out.append(dict(n_per_axis=n, tau=0.7, periodic=(1, 1, 1), solid=solid, chi_mask=chi, eps_mask=1e-8,
+                        force=(1e-5, 0, 0), chi_max=chi, eps=1e-7, precision=1, hadamard=0, sweeps=2,
+                        modes=synth.fourier_modes(31, i, kmax=4, amp_rho=1e-3, amp_u=1e-3), conserve_mass=True))
+    return out
+
+
+def mixed_batch_measurement(warmup=1, steps=2):
+    """The uneven batch stepped in one graph against the same simulations
+    stepped one after another (one step each, after one untimed step)."""
+    import paper_2512_07615_gb300 as tl
+    cfgs = mixed_batch_configs()
+    cells = sum((1 << c["n_per_axis"]) ** 3 for c in cfgs)
+    b = tl.Batch(cfgs)
+    info = b.info()
+    b.step(warmup)
+    ms = b.step_timed(steps) / steps
+    bonds = [s.stats()["max_bond"] for s in b.sims]
+    b.close()
+    alone = []
+    for c in cfgs:
+        c = dict(c)
+        n = c.pop("n_per_axis")
+        s = tl.Sim(n, **c)
+        s.step(1)
+        alone.append(s.step_timed(1))
+        s.close()
+    return {"workload": "mixed8: sizes %s^3, chi %s cycling, sphere packs (even seeds) and vessels (odd seeds), "
+                        "FP32" % ("/".join(str(1 << n) for n in MIXED_SIZES), "/".join(map(str, MIXED_CHIS))),
+            "value": cells / (ms * 1e3), "unit": "MLUPS", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "launches_per_step": info["launches_per_step"], "jobs_per_step": info["jobs_per_step"],
+            "max_bonds": bonds, "unbatched_ms_per_round": sum(alone), "unbatched_ms_each": alone,
+            "unbatched_value": cells / (sum(alone) * 1e3)}
+
+
 def cpu_threads():
     try:
         import threadpoolctl
@@ -269,6 +327,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-mixed", action="store_true",
+                    help="also time the eight uneven simulations (64^3-256^3, chi 32-128) in one graph")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     N3 = float((1 << w["n"]) ** 3)
@@ -405,6 +465,9 @@ def main():
     batched = None
     if rank == 0 and not args.no_batched and args.workload == "porous128":
         batched = batched_measurement()
+    batched_mixed = None
+    if rank == 0 and args.batched_mixed:
+        batched_mixed = mixed_batch_measurement()
 
     if rank == 0:
         out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
@@ -416,7 +479,7 @@ def main():
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
                "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-               "batched": batched}
+               "batched": batched, "batched_mixed": batched_mixed}
         print(json.dumps(out))
     sim.close()
     if world > 1:

@@ -5,6 +5,7 @@ r_0 = r_L = 1 (Eq. MPS with binary physical indices).
 
 Functions and what they follow
   to_tensor        contraction of all cores (Eq. MPS)
+  entry            one entry of that contraction (Eq. MPS at fixed indices)
   tt_svd           left-to-right SVD construction with truncation (Eq. svd-comp)
   round_mps        left-orthogonalising QR sweep, then a right-to-left truncated
                    SVD sweep that truncates only at the canonical centre
@@ -57,6 +58,15 @@ def to_tensor(cores):
     for c in cores[1:]:
         t = np.tensordot(t, c, axes=(t.ndim - 1, 0))
     return t.reshape((2,) * len(cores))
+
+
+def entry(cores, bits):
+    """One entry T[bits_0, ..., bits_{L-1}] of Eq. MPS: the product of the
+    per-site matrices A_k[:, bits_k, :] (a 1 x 1 result)."""
+    v = np.ones((1,))
+    for c, b in zip(cores, bits):
+        v = v @ c[:, int(b), :]
+    return float(v[0])
 
 
 def norm(cores):

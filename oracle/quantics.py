@@ -21,6 +21,13 @@ def site_of(axis, level, dim=3):
     return dim * level + axis
 
 
+def site_bits(n_bits, cell):
+    """Binary index of every site for one cell (x, y, z): site k holds bit
+    (n-1 - k//dim) of axis k % dim (Eq. scale_ordering)."""
+    dim = len(cell)
+    return [(int(cell[k % dim]) >> (n_bits - 1 - k // dim)) & 1 for k in range(dim * n_bits)]
+
+
 def _perm(n_bits, dim):
     # axis of the reshaped dense array that holds site k
     return [(k % dim) * n_bits + k // dim for k in range(dim * n_bits)]

@@ -1514,24 +1514,33 @@ int tnlbm_profile_step(tnlbm_sim* s, double* ms, double* flops, int* launches, d
 // scratch), so that a launch holds the jobs of all of them.
 struct tnlbm_batch {
   std::vector<tnlbm_sim*> sims;
-  int prec = 0, n = 0, L = 0, sweeps = 2;
+  int prec = 0, sweeps = 2;
   Arena arena;
-  cudaStream_t s0 = nullptr, s1 = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t s0 = nullptr;
+  std::vector<cudaStream_t> sfit;  // one fit stream per chain length in the batch
+  cudaEvent_t ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  struct Level {
-    std::vector<RoundJob> rj;
+  std::vector<int> lens;           // distinct chain lengths L, ascending
+  struct FitGroup {                // the fit jobs of one chain length
     std::vector<FitJob> fj;
-    RoundJob* d_rj = nullptr;
     FitJob* d_fj = nullptr;
-    std::vector<int> rho0;       // simulations with a rho_0 node at this level
+  };
+  struct Level {
+    std::vector<RoundJob> rj;      // all simulations' rounding jobs (each carries its L)
+    std::vector<FitGroup> fg;      // indexed like lens
+    RoundJob* d_rj = nullptr;
+    std::vector<int> rho0;         // simulations with a rho_0 node at this level
   };
   std::vector<Level> levels;
   int* d_status = nullptr;
-  MpsRef* d_copy_src = nullptr;
-  MpsRef* d_copy_dst = nullptr;
-  int ncopy = 0;
+  struct CopyGroup {
+    MpsRef* d_src = nullptr;
+    MpsRef* d_dst = nullptr;
+    int n = 0;
+  };
+  std::vector<CopyGroup> copies;   // indexed like lens
   int launches_per_step = 0;
 };
 
@@ -1540,68 +1549,93 @@ namespace tn {
 template <typename T>
 static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
   int nl = 0;
+  const int ng = (int)b->lens.size();
   for (auto& lv : b->levels) {
     for (int si : lv.rho0) {
       tnlbm_sim* s = b->sims[si];
-      launch_rho0<T>(s->d_rho_ref, b->L, s->n_fluid, s->d_scal, b->s0);
+      launch_rho0<T>(s->d_rho_ref, s->L, s->n_fluid, s->d_scal, b->s0);
       ++nl;
     }
-    const bool both = !lv.rj.empty() && !lv.fj.empty();
-    if (both) {
+    bool any_fit = false;
+    for (auto& g : lv.fg) any_fit = any_fit || !g.fj.empty();
+    // fits of each chain length on their own stream, beside the level's roundings
+    if (any_fit) {
       cudaEventRecord(b->ev_fork, b->s0);
-      cudaStreamWaitEvent(b->s1, b->ev_fork, 0);
+      for (int gi = 0; gi < ng; ++gi)
+        if (!lv.fg[gi].fj.empty()) cudaStreamWaitEvent(b->sfit[gi], b->ev_fork, 0);
+      for (int gi = 0; gi < ng; ++gi) {
+        auto& g = lv.fg[gi];
+        if (g.fj.empty()) continue;
+        nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr);
+      }
     }
-    if (!lv.fj.empty())
-      nl += run_fit<T>(lv.d_fj, lv.fj, b->L, b->sweeps, b->d_status, both ? b->s1 : b->s0, nullptr);
     if (!lv.rj.empty()) {
-      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->L, b->n, nullptr, nullptr, b->d_status, b->s0);
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->lens.back(), 0, nullptr, nullptr, b->d_status, b->s0);
       ++nl;
     }
-    if (both) {
-      cudaEventRecord(b->ev_join, b->s1);
-      cudaStreamWaitEvent(b->s0, b->ev_join, 0);
-    }
+    if (any_fit)
+      for (int gi = 0; gi < ng; ++gi) {
+        if (lv.fg[gi].fj.empty()) continue;
+        cudaEventRecord(b->ev_join[gi], b->sfit[gi]);
+        cudaStreamWaitEvent(b->s0, b->ev_join[gi], 0);
+      }
   }
   for (tnlbm_sim* s : b->sims)
     if (s->cfg.conserve_mass) {
-      launch_mass_fix<T>(s->d_copy_src, s->lat.Q, b->L, s->d_mass, s->d_mass0, b->s0);
+      launch_mass_fix<T>(s->d_copy_src, s->lat.Q, s->L, s->d_mass, s->d_mass0, b->s0);
       nl += 2;
     }
-  launch_copy<T>(b->d_copy_src, b->d_copy_dst, b->ncopy, b->L, b->s0);
-  ++nl;
+  for (int gi = 0; gi < ng; ++gi) {
+    launch_copy<T>(b->copies[gi].d_src, b->copies[gi].d_dst, b->copies[gi].n, b->lens[gi], b->s0);
+    ++nl;
+  }
   *launches = nl;
   return 0;
 }
 
 template <typename T>
 static int batch_build(tnlbm_batch* b) {
+  for (tnlbm_sim* s : b->sims) b->lens.push_back(s->L);
+  std::sort(b->lens.begin(), b->lens.end());
+  b->lens.erase(std::unique(b->lens.begin(), b->lens.end()), b->lens.end());
+  const int ng = (int)b->lens.size();
+  auto group = [&](int L) { return (int)(std::lower_bound(b->lens.begin(), b->lens.end(), L) - b->lens.begin()); };
   TN_CUDA(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
-  TN_CUDA(cudaStreamCreateWithFlags(&b->s1, cudaStreamNonBlocking));
   TN_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
-  TN_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  b->sfit.assign(ng, nullptr);
+  b->ev_join.assign(ng, nullptr);
+  for (int gi = 0; gi < ng; ++gi) {
+    TN_CUDA(cudaStreamCreateWithFlags(&b->sfit[gi], cudaStreamNonBlocking));
+    TN_CUDA(cudaEventCreateWithFlags(&b->ev_join[gi], cudaEventDisableTiming));
+  }
   b->d_status = (int*)b->arena.alloc(STATUS_INTS * sizeof(int));
   if (!b->d_status) return TNLBM_E_OOM;
   TN_CUDA(cudaMemset(b->d_status, 0, STATUS_INTS * sizeof(int)));
   size_t nlev = 0;
   for (tnlbm_sim* s : b->sims) nlev = std::max(nlev, s->levels.size());
-  b->levels.assign(nlev, tnlbm_batch::Level{});
-  std::vector<MpsRef> src, dst;
+  tnlbm_batch::Level empty;
+  empty.fg.resize(ng);
+  b->levels.assign(nlev, empty);
+  std::vector<std::vector<MpsRef>> src(ng), dst(ng);
   for (int si = 0; si < (int)b->sims.size(); ++si) {
     tnlbm_sim* s = b->sims[si];
+    const int gi = group(s->L);
     for (size_t l = 0; l < s->levels.size(); ++l) {
       auto& in = s->levels[l];
       auto& out = b->levels[l];
       for (RoundJob rj : in.rj) {
         rj.masks = s->d_masks;
         rj.scal = s->d_scal;
+        rj.L = s->L;
+        rj.n_bits = s->n;
         out.rj.push_back(rj);
       }
-      for (const FitJob& fj : in.fj) out.fj.push_back(fj);
+      for (const FitJob& fj : in.fj) out.fg[gi].fj.push_back(fj);
       if (in.has_rho0) out.rho0.push_back(si);
     }
     for (int i = 0; i < s->lat.Q; ++i) {
-      src.push_back(s->nodes[s->f_next[i]]);
-      dst.push_back(s->nodes[s->f_state[i]]);
+      src[gi].push_back(s->nodes[s->f_next[i]]);
+      dst[gi].push_back(s->nodes[s->f_state[i]]);
     }
   }
   for (auto& lv : b->levels) {
@@ -1610,18 +1644,23 @@ static int batch_build(tnlbm_batch* b) {
       if (!lv.d_rj) return TNLBM_E_OOM;
       TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
     }
-    if (!lv.fj.empty()) {
-      lv.d_fj = (FitJob*)b->arena.alloc(lv.fj.size() * sizeof(FitJob));
-      if (!lv.d_fj) return TNLBM_E_OOM;
-      TN_CUDA(cudaMemcpy(lv.d_fj, lv.fj.data(), lv.fj.size() * sizeof(FitJob), cudaMemcpyHostToDevice));
+    for (auto& g : lv.fg) {
+      if (g.fj.empty()) continue;
+      g.d_fj = (FitJob*)b->arena.alloc(g.fj.size() * sizeof(FitJob));
+      if (!g.d_fj) return TNLBM_E_OOM;
+      TN_CUDA(cudaMemcpy(g.d_fj, g.fj.data(), g.fj.size() * sizeof(FitJob), cudaMemcpyHostToDevice));
     }
   }
-  b->ncopy = (int)src.size();
-  b->d_copy_src = (MpsRef*)b->arena.alloc(src.size() * sizeof(MpsRef));
-  b->d_copy_dst = (MpsRef*)b->arena.alloc(dst.size() * sizeof(MpsRef));
-  if (!b->d_copy_src || !b->d_copy_dst) return TNLBM_E_OOM;
-  TN_CUDA(cudaMemcpy(b->d_copy_src, src.data(), src.size() * sizeof(MpsRef), cudaMemcpyHostToDevice));
-  TN_CUDA(cudaMemcpy(b->d_copy_dst, dst.data(), dst.size() * sizeof(MpsRef), cudaMemcpyHostToDevice));
+  b->copies.assign(ng, tnlbm_batch::CopyGroup{});
+  for (int gi = 0; gi < ng; ++gi) {
+    auto& c = b->copies[gi];
+    c.n = (int)src[gi].size();
+    c.d_src = (MpsRef*)b->arena.alloc(c.n * sizeof(MpsRef));
+    c.d_dst = (MpsRef*)b->arena.alloc(c.n * sizeof(MpsRef));
+    if (!c.d_src || !c.d_dst) return TNLBM_E_OOM;
+    TN_CUDA(cudaMemcpy(c.d_src, src[gi].data(), c.n * sizeof(MpsRef), cudaMemcpyHostToDevice));
+    TN_CUDA(cudaMemcpy(c.d_dst, dst[gi].data(), c.n * sizeof(MpsRef), cudaMemcpyHostToDevice));
+  }
   TN_CUDA(cudaDeviceSynchronize());
   TN_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
   int launches = 0;
@@ -1652,9 +1691,11 @@ int tnlbm_batch_destroy(tnlbm_batch* b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
-  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  for (cudaEvent_t e : b->ev_join)
+    if (e) cudaEventDestroy(e);
   if (b->s0) cudaStreamDestroy(b->s0);
-  if (b->s1) cudaStreamDestroy(b->s1);
+  for (cudaStream_t st : b->sfit)
+    if (st) cudaStreamDestroy(st);
   for (tnlbm_sim* s : b->sims) tnlbm_destroy(s);
   delete b;
   return 0;
@@ -1665,9 +1706,8 @@ int tnlbm_batch_create(const tnlbm_config* cfgs, int nsim, tnlbm_batch** out) {
   *out = nullptr;
   if (!cfgs || nsim < 1 || nsim > 64) { set_error("bad arguments to tnlbm_batch_create"); return TNLBM_E_ARG; }
   for (int i = 1; i < nsim; ++i)
-    if (cfgs[i].n_per_axis != cfgs[0].n_per_axis || cfgs[i].precision != cfgs[0].precision ||
-        std::max(cfgs[i].sweeps, 0) != std::max(cfgs[0].sweeps, 0)) {
-      set_error("batched simulations need the same n_per_axis, precision and fit sweeps");
+    if (cfgs[i].precision != cfgs[0].precision || std::max(cfgs[i].sweeps, 0) != std::max(cfgs[0].sweeps, 0)) {
+      set_error("batched simulations need the same precision and fit sweeps");
       return TNLBM_E_ARG;
     }
   tnlbm_batch* b = new (std::nothrow) tnlbm_batch();
@@ -1683,8 +1723,6 @@ int tnlbm_batch_create(const tnlbm_config* cfgs, int nsim, tnlbm_batch** out) {
     }
     b->sims.push_back(s);
   }
-  b->n = b->sims[0]->n;
-  b->L = b->sims[0]->L;
   b->prec = b->sims[0]->prec;
   b->sweeps = b->sims[0]->cfg.sweeps;
   int rc = b->prec == TNLBM_FP64 ? tn::batch_build<double>(b) : tn::batch_build<float>(b);
@@ -1735,7 +1773,10 @@ int tnlbm_batch_info(tnlbm_batch* b, int* nsim, int* launches_per_step, int* job
   if (launches_per_step) *launches_per_step = b->launches_per_step;
   if (jobs_per_step) {
     int j = 0;
-    for (auto& lv : b->levels) j += (int)(lv.rj.size() + lv.fj.size());
+    for (auto& lv : b->levels) {
+      j += (int)lv.rj.size();
+      for (auto& g : lv.fg) j += (int)g.fj.size();
+    }
     *jobs_per_step = j;
   }
   return 0;

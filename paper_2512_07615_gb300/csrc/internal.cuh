@@ -131,6 +131,7 @@ struct RoundJob {
   JobLog* log;                // spectra of the previous step (modes 2 and logging), or null
   const void* masks;          // T*, rank-1 mask table of this job's simulation, or null = launch's
   const double* scal;         // scalars of this job's simulation, or null = launch's
+  int L, n_bits;              // chain length and bits per axis of this job, or 0 = launch's
 };
 
 // bound of one term's bond k from the capacities of its operands

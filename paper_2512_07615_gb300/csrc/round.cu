@@ -198,14 +198,17 @@ struct PhaseClock {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L,
-                                                   int n_bits, const T* __restrict__ masks_arg,
+__global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L_arg,
+                                                   int n_bits_arg, const T* __restrict__ masks_arg,
                                                    const double* __restrict__ scal_arg,
                                                    int* __restrict__ status,
                                                    double* __restrict__ ctr,
                                                    const LearnCtx* __restrict__ lc) {
   const RoundJob& J = jobs[blockIdx.x];
-  // per-job mask table and scalars (jobs of several simulations in one launch)
+  // per-job chain length, mask table and scalars (jobs of several simulations,
+  // possibly of different lattice sizes, in one launch)
+  const int L = J.L > 0 ? J.L : L_arg;
+  const int n_bits = J.n_bits > 0 ? J.n_bits : n_bits_arg;
   const T* __restrict__ masks = J.masks ? (const T*)J.masks : masks_arg;
   const double* __restrict__ scal = J.scal ? J.scal : scal_arg;
   extern __shared__ __align__(16) unsigned char smem[];

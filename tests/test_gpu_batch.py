@@ -66,8 +66,36 @@ def test_batch_timed_steps_and_borrowed_handles(tl):
     b.close()
 
 
-def test_batch_rejects_mixed_sizes(tl):
+def test_batch_of_uneven_sizes_equals_simulations_alone(tl):
+    """Simulations of 8^3, 16^3 and 32^3 with different chi in one graph: the
+    rounding launches mix jobs of different chain lengths, the fits of each
+    length run on their own stream."""
+    cfgs = [
+        dict(n_per_axis=3, tau=0.8, periodic=(1, 1, 0), force=(1e-5, 0, 0), chi_max=8, eps=1e-7,
+             precision=1, hadamard=0, modes=synth.fourier_modes(2, 1, kmax=1, amp_rho=1e-3, amp_u=1e-2)),
+        dict(n_per_axis=5, tau=0.7, periodic=(1, 1, 1), solid=synth.sphere_pack(5, 4.0, 0.25, 1), chi_mask=16,
+             eps_mask=1e-8, force=(1e-5, 0, 0), chi_max=32, eps=1e-7, precision=1, hadamard=0, conserve_mass=True),
+        configs()[0],
+        dict(n_per_axis=5, tau=0.9, periodic=(1, 1, 1), solid=synth.vessel_tree(5, 3.0, 2, 3), chi_mask=16,
+             eps_mask=1e-8, force=(1e-5, 0, 0), chi_max=16, eps=1e-7, precision=1, hadamard=0),
+    ]
+    b = tl.Batch(cfgs)
+    b.step(3)
+    got = [s.macroscopic() for s in b.sims]
+    for i, kw in enumerate(cfgs):
+        kw = dict(kw)
+        n = kw.pop("n_per_axis")
+        alone = tl.Sim(n, **kw)
+        alone.step(3)
+        rho, u = alone.macroscopic()
+        alone.close()
+        assert np.array_equal(rho, got[i][0]) and np.array_equal(u, got[i][1]), i
+        assert b.sims[i].stats()["status"] == 0
+    b.close()
+
+
+def test_batch_rejects_mixed_precision(tl):
     cfgs = configs()[:2]
-    cfgs[1] = dict(cfgs[1], n_per_axis=3, solid=synth.sphere_pack(3, 1.5, 0.25, 2))
+    cfgs[1] = dict(cfgs[1], precision=0)
     with pytest.raises(tl.nat.TnlbmError):
         tl.Batch(cfgs)

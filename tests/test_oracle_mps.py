@@ -109,3 +109,12 @@ def test_fit_close_to_svd_truncation():
     e_fit = np.linalg.norm(fit - exact)
     e_rnd = np.linalg.norm(rnd - exact)
     assert e_fit <= 3.0 * e_rnd + 1e-14 * np.linalg.norm(exact)
+
+
+def test_entry_equals_contracted_tensor():
+    A = _rand(7, 5, 11)
+    T = M.to_tensor(A)
+    rng = np.random.default_rng(4)
+    for _ in range(40):
+        bits = rng.integers(0, 2, 7)
+        assert abs(M.entry(A, bits) - T[tuple(bits)]) <= 1e-13 * np.abs(T).max()

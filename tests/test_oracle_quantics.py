@@ -29,3 +29,15 @@ def test_bit_positions():
             assert bits[3 * lev + 1] == (y >> (n - 1 - lev)) & 1
             assert bits[3 * lev + 2] == (z >> (n - 1 - lev)) & 1
         assert q.site_of(2, 1) == 5
+
+
+def test_site_bits_index_the_encoded_tensor():
+    # every cell of a random field is found at its site bits in the encoded tensor
+    rng = np.random.default_rng(3)
+    n, N = 3, 8
+    a = rng.standard_normal((N, N, N))
+    t = q.encode(a)
+    for x in range(N):
+        for y in range(N):
+            for z in range(N):
+                assert t[tuple(q.site_bits(n, (x, y, z)))] == a[x, y, z]
