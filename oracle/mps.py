@@ -15,6 +15,8 @@ Functions and what they follow
   apply_mpo        site-wise MPO x MPS contraction (Eq. applympo)
   inner_ones       contraction with the rank-1 all-ones MPS (Sec. 3.2, rho_0)
   hadamard_fit     compressed product by single-site variational fit (Sec. 2.3)
+  zipup_pass,      compressed product by one left-to-right zip-up pass, then
+  hadamard_zipup   a rounding (the alternative to the fit that Sec. 2.3 names)
 
 Truncation rule (the paper fixes only chi): at each bond keep the smallest
 r <= chi_max with sqrt(sum_{j>=r} s_j^2) <= eps * ||T|| / sqrt(L-1), r >= 1.
@@ -308,3 +310,48 @@ def hadamard_fit(B, C, sweeps=2, record=None):
                 A[c - 1] = np.tensordot(A[c - 1], R.T, axes=(2, 0))
                 ER[c] = _env_right(ER[c + 1], A[c], B[c], C[c])
     return A
+
+
+def zipup_pass(B, C, chi_max, eps):
+    """One left-to-right zip-up pass over the element-wise product B * C (the
+    alternative to the fit named in Sec. 2.3).  A matrix M carries the product
+    bond (b, c) of the sites done so far to the new bond a.  At site k the
+    product core is contracted into it,
+        T[a, s, c', b'] = sum_{b, c} M[a, c, b] B_k[b, s, b'] C_k[c, s, c'],
+    T is unfolded as (a s) x (c' b') and factorised by a truncated SVD: U (rank
+    r) is the new core, M = S_r V_r^T is carried on.  The last site keeps T.
+    Truncation: choose_rank with delta = eps ||T_0|| / sqrt(L-1), T_0 the
+    first site's unfolding.  The result is left-orthogonal up to its last
+    core.  With C the all-ones MPS (rank 1, cores [1, 1]) this is the
+    left-to-right truncated SVD sweep of B (Eq. svd-move run rightwards)."""
+    L = len(B)
+    M = np.ones((1, 1, 1))
+    delta = None
+    out = []
+    for k in range(L):
+        X = np.einsum("acb,bsy->acsy", M, B[k], optimize=True)
+        T = np.einsum("acsy,csz->aszy", X, C[k], optimize=True)
+        a, _, z, y = T.shape
+        Tm = T.reshape(a * 2, z * y)
+        if delta is None:
+            delta = eps * float(np.sqrt(np.sum(Tm * Tm))) / np.sqrt(max(L - 1, 1))
+        if k == L - 1:
+            out.append(Tm.reshape(a, 2, 1))
+            break
+        U, S, Vt = np.linalg.svd(Tm, full_matrices=False)
+        r = choose_rank(S, chi_max, delta)
+        out.append(U[:, :r].reshape(a, 2, r))
+        M = (S[:r, None] * Vt[:r]).reshape(r, z, y)
+    return out
+
+
+def hadamard_zipup(B, C, chi_max, eps):
+    """Compressed product by the zip-up pass.  Both factors are first brought
+    to right-canonical form (right_orthogonalize: the truncation at each site
+    then sees orthonormal rows of each factor's remaining sites; without it
+    the pass can lose most of the product), then the pass, then a rounding
+    of its result (round_mps: the QR sweep finds the pass's cores already
+    left-orthogonal; the right-to-left SVD sweep truncates at the centre and
+    leaves the centre at site 0, as the fit and every rounding do)."""
+    Z = zipup_pass(right_orthogonalize(B), right_orthogonalize(C), chi_max, eps)
+    return round_mps(Z, chi_max, eps)

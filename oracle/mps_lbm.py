@@ -24,8 +24,9 @@ Every population f_i is an MPS on L = 3n binary sites (Sec. 2.4).  One step:
  a9 rounding     every sum above is rounded with oracle.mps.round_mps
 
 Products "*" use the single-site fit of Sec. 2.3 with the first factor as the
-candidate (hadamard='fit'), or the exact Kronecker product of Eq. (mul) followed
-by a rounding (hadamard='exact').
+candidate (hadamard='fit'), the exact Kronecker product of Eq. (mul) followed
+by a rounding (hadamard='exact'), or the zip-up pass followed by a rounding
+(hadamard='zipup', oracle.mps.hadamard_zipup).
 
 Order of the linear combinations in a6 (the paper does not fix it): shared
 partial sums are formed once and reused.
@@ -86,6 +87,8 @@ def _R(cfg, terms):
 def _had(cfg, B, C):
     if cfg.hadamard == "fit":
         return M.hadamard_fit(B, C, sweeps=cfg.sweeps)
+    if cfg.hadamard == "zipup":
+        return M.hadamard_zipup(B, C, cfg.chi, cfg.eps)
     return M.round_mps(M.hadamard_exact(B, C), cfg.chi, cfg.eps)
 
 
