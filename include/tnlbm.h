@@ -53,7 +53,7 @@ enum {
 
 enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1 };
 enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
-enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1 };
+enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1, TNLBM_HADAMARD_ZIPUP = 2 };
 
 /* ------------------------------------------------------------ simulation */
 
@@ -79,8 +79,9 @@ typedef struct {
   double eps;              /* relative rounding tolerance: keep the smallest
                               rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
   int precision;           /* TNLBM_FP64 or TNLBM_FP32                         */
-  int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default) or _EXACT
-                              (Eq. mul followed by a rounding)                  */
+  int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default), _EXACT
+                              (Eq. mul followed by a rounding) or _ZIPUP (the
+                              zip-up pass, then a rounding; chi_max <= 512)     */
   int sweeps;              /* round trips of the product fit (Sec. 2.3: 2)     */
   int n_modes;             /* 0: start at rest, f_i = w_i (1 - m_O);  > 0:
                               f_i = w_i (1 + sum_m (a_rho + 3 c_i.a_u) cos(2 pi
@@ -157,7 +158,7 @@ int tnlbm_step_timed(tnlbm_sim *s, int k, double *ms);
 
 /* Kernel classes reported by tnlbm_profile_step (array index). */
 enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_MISC = 3,
-       TNLBM_K_RHO0 = 4, TNLBM_K_COPY = 5, TNLBM_K_COUNT = 6 };
+       TNLBM_K_RHO0 = 4, TNLBM_K_COPY = 5, TNLBM_K_ZIPUP = 6, TNLBM_K_COUNT = 7 };
 
 /* Advance one step with eager (non-graph), serialised launches and report per
  * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
@@ -235,6 +236,21 @@ int tnlbm_lincomb_round_noalloc(int precision, int n_bits, int batch, int nterms
 int tnlbm_materialize(int precision, int n_bits, int batch,
                       const tnlbm_term *terms, void *const *dst,
                       int *const *dst_ranks, int dst_cap, void *stream);
+
+/* A[b] ~ B[b] . C[b] by the zip-up pass, the alternative to the fit that
+ * Sec. 2.3 names: copies of B and C are brought to right-canonical form, one
+ * left-to-right pass contracts each site's product core into the carried
+ * matrix and truncates it (QR of the unfolding, Jacobi SVD of R, chi_max and
+ * the tail rule with delta = eps ||T_0|| / sqrt(L-1), T_0 the first site's
+ * unfolding), and the result is rounded (chi_max, eps) into A.  Caps of B and
+ * C <= 512, chi_max <= 512, capA >= chi_max; B and C are not modified.
+ * Allocates its scratch (cudaMalloc) and synchronises `stream`.
+ * Not in the paper's own runs (it uses the fit). */
+int tnlbm_hadamard_zipup(int precision, int n_bits, int batch,
+                         const void *const *B, const int *const *rB, int capB,
+                         const void *const *C, const int *const *rC, int capC,
+                         void *const *A, int *const *rA, int capA, int chi_max,
+                         double eps, void *stream);
 
 /* A[b] ~ B[b] . C[b] by the single-site variational fit of Sec. 2.3: candidate
  * A = B (bonds unchanged), `sweeps` round trips of local updates and QR/LQ

@@ -100,7 +100,7 @@ struct TermSpec {       // host-side description of a term, resolved to MpsRef a
 };
 
 struct JobSpec {
-  int kind;             // 0 rounding, 1 fit, 2 rho0 scalar
+  int kind;             // 0 rounding, 1 fit, 2 rho0 scalar, 3 zip-up pass
   int out;              // node id
   std::vector<TermSpec> terms;
   int b = -1, c = -1;   // fit factors
@@ -139,8 +139,10 @@ struct tnlbm_sim {
   struct Level {
     std::vector<RoundJob> rj;
     std::vector<FitJob> fj;
+    std::vector<ZipJob> zj;
     RoundJob* d_rj = nullptr;
     FitJob* d_fj = nullptr;
+    ZipJob* d_zj = nullptr;
     bool has_rho0 = false;
   };
   std::vector<Level> levels;
@@ -211,6 +213,15 @@ struct Builder {
     if (s->cfg.hadamard == TNLBM_HADAMARD_EXACT) {
       TermSpec t; t.kind = T_KRON; t.x = b; t.y = c;
       return R({t});
+    }
+    if (s->cfg.hadamard == TNLBM_HADAMARD_ZIPUP) {      // zip-up pass, then a rounding
+      int lv = std::max(s->node_level[b], s->node_level[c]) + 1;
+      int z = new_node(s, chi(), lv);
+      if (z < 0) { oom = true; return -1; }
+      JobSpec j;
+      j.kind = 3; j.out = z; j.b = b; j.c = c; j.level = lv;
+      s->specs.push_back(j);
+      return R({P(z, 1.0)});
     }
     int lv = std::max(s->node_level[b], s->node_level[c]) + 1;
     int out = new_node(s, s->nodes[b].cap, lv);
@@ -476,6 +487,15 @@ static int upload_levels(tnlbm_sim* s) {
       plan_round_job(rj, s->L, s->n, sizeof(T));
       lvl_round[js.level] += rj.lay.total;
       lv.rj.push_back(rj);
+    } else if (js.kind == 3) {
+      ZipJob zj{};
+      zj.B = s->nodes[js.b];
+      zj.C = s->nodes[js.c];
+      zj.Z = s->nodes[js.out];
+      zj.chi = s->cfg.chi_max;
+      zj.eps = s->cfg.eps;
+      lvl_fit[js.level] += zip_scratch_elems(s->L, zj.B.cap, zj.C.cap, zj.Z.cap, sizeof(T));
+      lv.zj.push_back(zj);
     } else {
       FitJob fj{};
       fj.A = s->nodes[js.out];
@@ -510,6 +530,15 @@ static int upload_levels(tnlbm_sim* s) {
       fj.abuf = fbase + o; o += ab;
       fj.qscr = fbase + o; o += 4 * q;
     }
+    for (auto& zj : lv.zj) {
+      zj.scratch = fbase + o;
+      o += zip_scratch_elems(s->L, zj.B.cap, zj.C.cap, zj.Z.cap, sizeof(T));
+    }
+    if (!lv.zj.empty()) {
+      lv.d_zj = (ZipJob*)s->arena.alloc(lv.zj.size() * sizeof(ZipJob));
+      if (!lv.d_zj) return TNLBM_E_OOM;
+      cudaMemcpy(lv.d_zj, lv.zj.data(), lv.zj.size() * sizeof(ZipJob), cudaMemcpyHostToDevice);
+    }
     if (!lv.rj.empty()) {
       lv.d_rj = (RoundJob*)s->arena.alloc(lv.rj.size() * sizeof(RoundJob));
       if (!lv.d_rj) return TNLBM_E_OOM;
@@ -534,13 +563,18 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
       if (prof) prof->mark(C_RHO0);
       ++n;
     }
-    const bool both = !prof && !lv.rj.empty() && !lv.fj.empty();   // profiled runs stay serial
+    const bool side = !lv.fj.empty() || !lv.zj.empty();
+    const bool both = !prof && !lv.rj.empty() && side;   // profiled runs stay serial
     if (both) {
       cudaEventRecord(s->ev_fork, s->s0);
       cudaStreamWaitEvent(s->s1, s->ev_fork, 0);
     }
     if (!lv.fj.empty())
       n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof);
+    if (!lv.zj.empty()) {
+      n += run_zipup<T>(lv.d_zj, (int)lv.zj.size(), s->L, s->d_status, both ? s->s1 : s->s0, ctr);
+      if (prof) prof->mark(C_ZIPUP);
+    }
     if (!lv.rj.empty()) {
       launch_round<T>(lv.d_rj, (int)lv.rj.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal,
                       s->d_status, s->s0, ctr, s->learn_mode ? s->d_learn : nullptr);
@@ -893,7 +927,11 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (C.chi_max < 1 || C.chi_max > 512) { set_error("chi_max must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.eps < 0.0) { set_error("eps must be >= 0"); return TNLBM_E_ARG; }
   if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32) { set_error("bad precision"); return TNLBM_E_ARG; }
-  if (C.hadamard != TNLBM_HADAMARD_FIT && C.hadamard != TNLBM_HADAMARD_EXACT) { set_error("bad hadamard mode"); return TNLBM_E_ARG; }
+  if (C.hadamard != TNLBM_HADAMARD_FIT && C.hadamard != TNLBM_HADAMARD_EXACT && C.hadamard != TNLBM_HADAMARD_ZIPUP) {
+    set_error("bad hadamard mode");
+    return TNLBM_E_ARG;
+  }
+  if (C.hadamard == TNLBM_HADAMARD_ZIPUP && C.chi_max > 512) { set_error("zip-up products need chi_max <= 512"); return TNLBM_E_ARG; }
   if (C.solid && C.mask_cores) { set_error("give solid voxels or mask cores, not both"); return TNLBM_E_ARG; }
   if (C.mask_cores && (!C.mask_ranks || C.mask_cap < 1)) { set_error("mask_ranks / mask_cap missing"); return TNLBM_E_ARG; }
   if (C.solid && (C.chi_mask < 1 || C.chi_mask > 512)) { set_error("chi_mask must be in [1, 512]"); return TNLBM_E_ARG; }
@@ -1316,6 +1354,59 @@ static int fit_impl(int n_bits, int batch, const void* const* B, const int* cons
   return check_status((int*)ds.p, st);
 }
 
+template <typename T>
+static int zipup_impl(int n_bits, int batch, const void* const* B, const int* const* rB, int capB,
+                      const void* const* C, const int* const* rC, int capC, void* const* A, int* const* rA,
+                      int capA, int chi, double eps, cudaStream_t st) {
+  const int L = 3 * n_bits;
+  std::vector<ZipJob> zj(batch);
+  std::vector<RoundJob> rj(batch);
+  const size_t zs = zip_scratch_elems(L, capB, capC, chi, sizeof(T));
+  const size_t zm = mps_size(L, chi);
+  DevBuf zscr, ztmp, zrk, dz, dr, ds, rscr;
+  if (!zscr.alloc((size_t)batch * zs * sizeof(T)) || !ztmp.alloc((size_t)batch * zm * sizeof(T)) ||
+      !zrk.alloc((size_t)batch * (L + 1) * sizeof(int)) || !dz.alloc(batch * sizeof(ZipJob)) ||
+      !dr.alloc(batch * sizeof(RoundJob)) || !ds.alloc(STATUS_INTS * sizeof(int))) {
+    set_error("out of device memory");
+    return TNLBM_E_OOM;
+  }
+  size_t rtot = 0;
+  for (int b = 0; b < batch; ++b) {
+    ZipJob& z = zj[b];
+    z = ZipJob{};
+    z.B.base = (void*)B[b]; z.B.ranks = (int*)rB[b]; z.B.cap = capB;
+    z.C.base = (void*)C[b]; z.C.ranks = (int*)rC[b]; z.C.cap = capC;
+    z.Z.base = (T*)ztmp.p + (size_t)b * zm; z.Z.ranks = (int*)zrk.p + (size_t)b * (L + 1); z.Z.cap = chi;
+    z.chi = chi;
+    z.eps = eps;
+    z.scratch = (T*)zscr.p + (size_t)b * zs;
+    RoundJob& r = rj[b];
+    r = RoundJob{};
+    r.nterms = 1;
+    r.chi = chi;
+    r.eps = eps;
+    r.t[0] = Term{};
+    r.t[0].kind = T_PLAIN;
+    r.t[0].coef = 1.0;
+    r.t[0].coef_slot = -1;
+    r.t[0].mask_id = -1;
+    r.t[0].x = z.Z;
+    r.dst.base = A[b]; r.dst.ranks = rA[b]; r.dst.cap = capA;
+    plan_round_job(r, L, n_bits, sizeof(T));
+    rtot += r.lay.total;
+  }
+  if (!rscr.alloc(rtot * sizeof(T))) { set_error("out of device memory"); return TNLBM_E_OOM; }
+  size_t o = 0;
+  for (auto& r : rj) { r.scratch = (T*)rscr.p + o; o += r.lay.total; }
+  TN_CUDA(cudaMemcpyAsync(dz.p, zj.data(), batch * sizeof(ZipJob), cudaMemcpyHostToDevice, st));
+  TN_CUDA(cudaMemcpyAsync(dr.p, rj.data(), batch * sizeof(RoundJob), cudaMemcpyHostToDevice, st));
+  TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
+  run_zipup<T>((const ZipJob*)dz.p, batch, L, (int*)ds.p, st);
+  launch_round<T>((const RoundJob*)dr.p, batch, L, n_bits, nullptr, nullptr, (int*)ds.p, st);
+  TN_CUDA(cudaGetLastError());
+  return check_status((int*)ds.p, st);
+}
+
 }  // namespace tn
 
 extern "C" {
@@ -1370,6 +1461,21 @@ int tnlbm_materialize(int precision, int n_bits, int batch, const tnlbm_term* te
   return precision == TNLBM_FP64
              ? tn::lincomb_impl<double>(n_bits, batch, 1, terms, dst, dst_ranks, dst_cap, 1, 0.0, 1, st)
              : tn::lincomb_impl<float>(n_bits, batch, 1, terms, dst, dst_ranks, dst_cap, 1, 0.0, 1, st);
+}
+
+int tnlbm_hadamard_zipup(int precision, int n_bits, int batch, const void* const* B, const int* const* rB,
+                         int capB, const void* const* C, const int* const* rC, int capC, void* const* A,
+                         int* const* rA, int capA, int chi_max, double eps, void* stream) {
+  if (n_bits < 1 || n_bits > 10 || batch < 0 || !B || !rB || !C || !rC || !A || !rA || capB < 1 || capC < 1 ||
+      capB > 512 || capC > 512 || chi_max < 1 || chi_max > 512 || capA < chi_max || eps < 0) {
+    set_error("bad arguments to tnlbm_hadamard_zipup");
+    return TNLBM_E_ARG;
+  }
+  if (batch == 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  return precision == TNLBM_FP64
+             ? tn::zipup_impl<double>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, chi_max, eps, st)
+             : tn::zipup_impl<float>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, chi_max, eps, st);
 }
 
 int tnlbm_hadamard_fit(int precision, int n_bits, int batch, const void* const* B, const int* const* rB,
@@ -1523,9 +1629,11 @@ struct tnlbm_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<int> lens;           // distinct chain lengths L, ascending
-  struct FitGroup {                // the fit jobs of one chain length
+  struct FitGroup {                // the fit and zip-up jobs of one chain length
     std::vector<FitJob> fj;
     FitJob* d_fj = nullptr;
+    std::vector<ZipJob> zj;
+    ZipJob* d_zj = nullptr;
   };
   struct Level {
     std::vector<RoundJob> rj;      // all simulations' rounding jobs (each carries its L)
@@ -1557,16 +1665,17 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
       ++nl;
     }
     bool any_fit = false;
-    for (auto& g : lv.fg) any_fit = any_fit || !g.fj.empty();
+    for (auto& g : lv.fg) any_fit = any_fit || !g.fj.empty() || !g.zj.empty();
     // fits of each chain length on their own stream, beside the level's roundings
     if (any_fit) {
       cudaEventRecord(b->ev_fork, b->s0);
       for (int gi = 0; gi < ng; ++gi)
-        if (!lv.fg[gi].fj.empty()) cudaStreamWaitEvent(b->sfit[gi], b->ev_fork, 0);
+        if (!lv.fg[gi].fj.empty() || !lv.fg[gi].zj.empty()) cudaStreamWaitEvent(b->sfit[gi], b->ev_fork, 0);
       for (int gi = 0; gi < ng; ++gi) {
         auto& g = lv.fg[gi];
-        if (g.fj.empty()) continue;
-        nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr);
+        if (!g.fj.empty()) nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr);
+        if (!g.zj.empty())
+          nl += run_zipup<T>(g.d_zj, (int)g.zj.size(), b->lens[gi], b->d_status, b->sfit[gi], nullptr);
       }
     }
     if (!lv.rj.empty()) {
@@ -1575,7 +1684,7 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
     }
     if (any_fit)
       for (int gi = 0; gi < ng; ++gi) {
-        if (lv.fg[gi].fj.empty()) continue;
+        if (lv.fg[gi].fj.empty() && lv.fg[gi].zj.empty()) continue;
         cudaEventRecord(b->ev_join[gi], b->sfit[gi]);
         cudaStreamWaitEvent(b->s0, b->ev_join[gi], 0);
       }
@@ -1631,6 +1740,7 @@ static int batch_build(tnlbm_batch* b) {
         out.rj.push_back(rj);
       }
       for (const FitJob& fj : in.fj) out.fg[gi].fj.push_back(fj);
+      for (const ZipJob& zj : in.zj) out.fg[gi].zj.push_back(zj);
       if (in.has_rho0) out.rho0.push_back(si);
     }
     for (int i = 0; i < s->lat.Q; ++i) {
@@ -1649,6 +1759,12 @@ static int batch_build(tnlbm_batch* b) {
       g.d_fj = (FitJob*)b->arena.alloc(g.fj.size() * sizeof(FitJob));
       if (!g.d_fj) return TNLBM_E_OOM;
       TN_CUDA(cudaMemcpy(g.d_fj, g.fj.data(), g.fj.size() * sizeof(FitJob), cudaMemcpyHostToDevice));
+    }
+    for (auto& g : lv.fg) {
+      if (g.zj.empty()) continue;
+      g.d_zj = (ZipJob*)b->arena.alloc(g.zj.size() * sizeof(ZipJob));
+      if (!g.d_zj) return TNLBM_E_OOM;
+      TN_CUDA(cudaMemcpy(g.d_zj, g.zj.data(), g.zj.size() * sizeof(ZipJob), cudaMemcpyHostToDevice));
     }
   }
   b->copies.assign(ng, tnlbm_batch::CopyGroup{});
@@ -1775,7 +1891,7 @@ int tnlbm_batch_info(tnlbm_batch* b, int* nsim, int* launches_per_step, int* job
     int j = 0;
     for (auto& lv : b->levels) {
       j += (int)lv.rj.size();
-      for (auto& g : lv.fg) j += (int)g.fj.size();
+      for (auto& g : lv.fg) j += (int)(g.fj.size() + g.zj.size());
     }
     *jobs_per_step = j;
   }

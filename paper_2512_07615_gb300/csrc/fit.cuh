@@ -20,6 +20,19 @@ struct FitJob {
 void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* y_elems,
                   size_t* abuf_elems, size_t* q_elems);
 
+// Zip-up product (zipup.cu): Z = the pass over B * C (left-orthogonal up to
+// its last core); the caller rounds Z afterwards.  Z.cap >= chi, caps <= 512.
+struct ZipJob {
+  MpsRef B, C, Z;
+  int chi;
+  double eps;
+  void* scratch;           // T*, zip_scratch_elems(L, B.cap, C.cap, Z.cap, sizeof(T))
+};
+size_t zip_scratch_elems(int L, int capB, int capC, int capZ, size_t esz);
+// One launch (one CTA per job); returns the number of launches.
+template <typename T>
+int run_zipup(const ZipJob* d_jobs, int njobs, int L, int* d_status, cudaStream_t st, double* d_ctr = nullptr);
+
 // Eager-launch profiler: an event after every launch on one stream; the time
 // between consecutive events is charged to the class of the launch.
 struct Prof {

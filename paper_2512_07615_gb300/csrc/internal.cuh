@@ -27,11 +27,12 @@ enum : int {
   ST_TIMEOUT = 8     // bounded wait ran out
 };
 // algorithmic FLOP counters per kernel class (profiling only; nullable)
-enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 = 4, C_COPY = 5, C_COUNT = 6 };
+enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 = 4, C_COPY = 5, C_ZIPUP = 6,
+             C_COUNT = 7 };
 // phases of the rounding kernel (cycles of thread 0, summed over jobs), stored
 // after the FLOP counters: terms, R*W GEMM, QR, Jacobi, SVD outputs, Q*US GEMM
 enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT = 4, PH_GEMM_C = 5, PH_COUNT = 10 };
-static constexpr int CTR_SIZE = 16;
+static constexpr int CTR_SIZE = 24;   // >= C_COUNT + PH_COUNT
 // Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
 __host__ __device__ inline double qr_flops(double m, double n) {
   const double k = m < n ? m : n, big = m < n ? n : m;

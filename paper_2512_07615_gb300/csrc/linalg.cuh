@@ -1013,6 +1013,7 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
     if (c == i) s_dneg[i] = neg ? 1 : 0;
   }
   __syncthreads();
+  if (Q == nullptr) return;                        // R only
   // ---- Q = (I - V_0 T_0 V_0^T) ... (I - V_last T_last V_last^T) [I; 0], backwards, in
   // place: X = A[p0:m, p0:kk] with the panel's columns reset to unit vectors
   for (int p0 = ((kk - 1) / QB) * QB; p0 >= 0; p0 -= QB) {

@@ -11,9 +11,9 @@ LIB_PATH = os.path.join(HERE, "libtnlbm.so")
 FP64, FP32 = 0, 1
 D3Q19, D3Q15 = 19, 15
 FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
-HADAMARD_FIT, HADAMARD_EXACT = 0, 1
+HADAMARD_FIT, HADAMARD_EXACT, HADAMARD_ZIPUP = 0, 1, 2
 TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
-KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy")
+KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy", "zipup")
 ROUND_PHASES = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus", "jacobi_sweeps", "svd_count",
                 "jacobi_global", "svd_global_count")
 
@@ -143,6 +143,11 @@ SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
                                           ctypes.c_int, ctypes.c_void_p]),
+    "tnlbm_hadamard_zipup": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     "tnlbm_inner_ones": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),

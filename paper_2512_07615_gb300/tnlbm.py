@@ -251,6 +251,17 @@ def hadamard_fit(B, C, A, sweeps=2, stream=None):
     nat.check(rc, "tnlbm_hadamard_fit")
 
 
+def hadamard_zipup(B, C, A, chi_max, eps, stream=None):
+    """A[b] ~ B[b] * C[b] by the zip-up pass and a rounding (tnlbm_hadamard_zipup)."""
+    p = A[0].precision
+    rc = nat.lib().tnlbm_hadamard_zipup(p, A[0].L // 3, len(A),
+                                        _ptrs([x.data for x in B]), _ptrs([x.ranks for x in B]), B[0].cap,
+                                        _ptrs([x.data for x in C]), _ptrs([x.ranks for x in C]), C[0].cap,
+                                        _ptrs([x.data for x in A]), _ptrs([x.ranks for x in A]), A[0].cap,
+                                        chi_max, eps, _stream(stream))
+    nat.check(rc, "tnlbm_hadamard_zipup")
+
+
 def inner_ones(X, stream=None):
     out = torch.zeros(len(X), dtype=torch.float64, device=X[0].data.device)
     rc = nat.lib().tnlbm_inner_ones(X[0].precision, X[0].L // 3, len(X), _ptrs([x.data for x in X]),
