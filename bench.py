@@ -425,9 +425,20 @@ def main():
     else:
         peak_tf, peak_src = 1.06, "measured FP64 DGEMM on this pool"
     launches = max(prof[dom]["launches"], 1)
+    # DRAM bytes of the rounding kernel: ncu (dram__bytes_read.sum +
+    # dram__bytes_write.sum) on the porous 64^3 workload at chi 64 measured
+    # 1.171 MB for a launch of 4 jobs; scaled by the jobs of an average
+    # launch here (each job reads its terms and writes its result).  Only for
+    # the FP32 chi-64 sphere packs it was measured on.
+    traffic = None
+    if dom == "round" and fp32 and w["chi"] == 64 and w["geometry"] == "spheres":
+        traffic = 1.171e6 / 4 * st["round_jobs_per_step"] / launches
     ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": None, "peak_source": peak_src,
+                "frac": ach / peak_tf, "traffic": traffic,
+                "traffic_source": ("ncu DRAM bytes per rounding job (porous 64^3, chi 64) x jobs per launch"
+                                   if traffic is not None else None),
+                "peak_source": peak_src,
                 "flops_per_launch": prof[dom]["flops"] / launches, "launches_per_step": prof[dom]["launches"],
                 "share_of_profiled_step": prof[dom]["ms"] / total_prof_ms if total_prof_ms else None,
                 "classes": {c: {"ms": round(v["ms"], 3), "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12

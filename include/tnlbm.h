@@ -125,6 +125,8 @@ typedef struct {
   double rho0;               /* last mean density rho_0 (Sec. 3.2)               */
   int status;                /* device status word (0 = fine)                    */
   int gpu_launches_per_step; /* kernels launched by one tnlbm_step(1)            */
+  int round_jobs_per_step;   /* rounding jobs (one CTA each) in one step         */
+  int product_jobs_per_step; /* fit or zip-up product jobs in one step           */
 } tnlbm_stats;
 
 /* Build a simulation: shift MPOs, mask MPS, initial populations, and a CUDA

@@ -1095,6 +1095,12 @@ int tnlbm_stats_get(tnlbm_sim* s, tnlbm_stats* out) {
   out->rho0 = scal[SC_RHO0];
   out->status = st;
   out->gpu_launches_per_step = s->launches_per_step;
+  out->round_jobs_per_step = 0;
+  out->product_jobs_per_step = 0;
+  for (auto& lv : s->levels) {
+    out->round_jobs_per_step += (int)lv.rj.size();
+    out->product_jobs_per_step += (int)(lv.fj.size() + lv.zj.size());
+  }
   return 0;
 }
 

@@ -60,6 +60,8 @@ class Stats(ctypes.Structure):
         ("rho0", ctypes.c_double),
         ("status", ctypes.c_int),
         ("gpu_launches_per_step", ctypes.c_int),
+        ("round_jobs_per_step", ctypes.c_int),
+        ("product_jobs_per_step", ctypes.c_int),
     ]
 
 
