@@ -307,6 +307,23 @@ def mixed_batch_measurement(warmup=1, steps=2):
             "unbatched_value": cells / (sum(alone) * 1e3)}
 
 
+def max_over_ranks(x, world, device):
+    """Max of a per-rank float over all ranks (replicas are timed by the
+    slowest one); identity for one process."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(ms, world, cells, steps):
+    """Whole-job represented MLUPS: every rank steps its own replica of
+    `cells` cells `steps` times; ms is the max over ranks of the timed region."""
+    return world * cells * steps / (ms / 1e3) / 1e6
+
+
 def cpu_threads():
     try:
         import threadpoolctl
@@ -404,12 +421,9 @@ def main():
         ms = sim.step_timed(args.steps)
     barrier()
     clocks = clk.summary()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, "cuda")
     st = sim.stats()
-    value = world * N3 * args.steps / (ms / 1e3) / 1e6
+    value = replica_value(ms, world, N3, args.steps)
     rho_end, _ = sim.macroscopic()
     mass_drift = abs(float(rho_end.sum()) - mass_start) / mass_start
 
@@ -463,8 +477,8 @@ def main():
             sim.step(1)
             pops = sim.get_populations()
         barrier()
-        el = time.perf_counter() - t
-        e2e = {"value": world * N3 * args.steps / el / 1e6, "unit": "MLUPS",
+        el_ms = max_over_ranks((time.perf_counter() - t) * 1e3, world, "cuda")
+        e2e = {"value": replica_value(el_ms, world, N3, args.steps), "unit": "MLUPS",
                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
 
     cpu = None
