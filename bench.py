@@ -441,12 +441,12 @@ def main():
     launches = max(prof[dom]["launches"], 1)
     # DRAM bytes of the rounding kernel: ncu (dram__bytes_read.sum +
     # dram__bytes_write.sum) on the porous 64^3 workload at chi 64 measured
-    # 1.171 MB for a launch of 4 jobs; scaled by the jobs of an average
+    # 1.156 MB for a launch of 4 jobs; scaled by the jobs of an average
     # launch here (each job reads its terms and writes its result).  Only for
     # the FP32 chi-64 sphere packs it was measured on.
     traffic = None
     if dom == "round" and fp32 and w["chi"] == 64 and w["geometry"] == "spheres":
-        traffic = 1.171e6 / 4 * st["round_jobs_per_step"] / launches
+        traffic = 1.156e6 / 4 * st["round_jobs_per_step"] / launches
     ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
     roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": ach / peak_tf, "traffic": traffic,

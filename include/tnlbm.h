@@ -127,6 +127,12 @@ typedef struct {
   int gpu_launches_per_step; /* kernels launched by one tnlbm_step(1)            */
   int round_jobs_per_step;   /* rounding jobs (one CTA each) in one step         */
   int product_jobs_per_step; /* fit or zip-up product jobs in one step           */
+  double mass;               /* sum of rho over all cells at the last rho_0 node
+                                (rho_0 * N_fluid)                                */
+  double discarded2;         /* sum over every rounding since creation of the
+                                squared norm discarded at each truncation
+                                (Eq. svd-move tails); difference two calls for
+                                a step's share                                  */
 } tnlbm_stats;
 
 /* Build a simulation: shift MPOs, mask MPS, initial populations, and a CUDA
@@ -141,6 +147,14 @@ int tnlbm_step(tnlbm_sim *s, int k);
  * rho[N^3] = sum_i f_i and u[3][N^3] = (sum_i c_i f_i + F (1 - m_O)/2) / rho
  * where rho > 0.5, else 0.  Either pointer may be NULL.  Synchronous. */
 int tnlbm_macroscopic(tnlbm_sim *s, double *rho, double *u);
+
+/* The plane coordinate[axis] = index (axis 0..2 = x, y, z) of the same
+ * fields, contracted from the MPS with that axis's sites fixed (no N^3 field
+ * is formed; for large N where rho and u do not fit host memory):
+ * rho[N^2], u[3][N^2], indexed [a][b] with a, b the two other coordinates in
+ * increasing axis order.  Host buffers, caller-owned; NULL skips a field.
+ * Synchronous. */
+int tnlbm_macroscopic_slice(tnlbm_sim *s, int axis, int index, double *rho, double *u);
 
 /* Populations as MPS: host buffers of Q * tnlbm_mps_size(L, chi_max) doubles
  * (flat layout, capacity chi_max, population-major) and Q*(L+1) ints.

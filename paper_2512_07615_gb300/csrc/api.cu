@@ -151,6 +151,7 @@ struct tnlbm_sim {
   MpsRef* d_copy_dst = nullptr;
   double* d_mass = nullptr;      // [Q] per-population masses (mass correction)
   double* d_mass0 = nullptr;     // initial total mass
+  double* d_discard = nullptr;   // squared discarded tails of all roundings so far
   int launches_per_step = 0;
   int64_t steps = 0;
   int pending_status = 0;
@@ -484,6 +485,7 @@ static int upload_levels(tnlbm_sim* s) {
         if (ts.y >= 0) tm.y = s->nodes[ts.y];
       }
       rj.dst = s->nodes[js.out];
+      rj.discard = s->d_discard;
       plan_round_job(rj, s->L, s->n, sizeof(T));
       lvl_round[js.level] += rj.lay.total;
       lv.rj.push_back(rj);
@@ -764,8 +766,10 @@ static int create_impl(tnlbm_sim* s) {
   TN_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
   s->d_scal = (double*)s->arena.alloc(SC_COUNT * sizeof(double));
   s->d_status = (int*)s->arena.alloc(STATUS_INTS * sizeof(int));
-  if (!s->d_scal || !s->d_status) return TNLBM_E_OOM;
+  s->d_discard = (double*)s->arena.alloc(sizeof(double));
+  if (!s->d_scal || !s->d_status || !s->d_discard) return TNLBM_E_OOM;
   cudaMemset(s->d_scal, 0, SC_COUNT * sizeof(double));
+  cudaMemset(s->d_discard, 0, sizeof(double));
   {
     double ub[18] = {0};                     // inlet velocities of the velocity faces
     for (int f6 = 0; f6 < 6; ++f6)
@@ -1023,6 +1027,37 @@ static int macro_impl(tnlbm_sim* s, double* rho, double* u) {
 }
 
 template <typename T>
+static int slice_impl(tnlbm_sim* s, int axis, int index, double* rho, double* u) {
+  using namespace tn;
+  const size_t nc = (size_t)s->N * s->N;
+  double *d = nullptr, *dm = nullptr, *tmp = nullptr;
+  void* scr = nullptr;
+  const int capmax = std::max(s->cfg.chi_max, s->mask_node >= 0 ? s->nodes[s->mask_node].cap : 1);
+  const size_t sb = plane_scratch_bytes(s->n, axis, capmax);
+  auto fin = [&](int rc) { cudaFree(d); cudaFree(dm); cudaFree(tmp); cudaFree(scr); return rc; };
+  if (cudaMalloc(&d, 4 * nc * sizeof(double)) != cudaSuccess || cudaMalloc(&tmp, nc * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&scr, sb) != cudaSuccess) {
+    set_error("out of device memory in tnlbm_macroscopic_slice");
+    return fin(TNLBM_E_OOM);
+  }
+  double *dr = d, *jx = d + nc, *jy = d + 2 * nc, *jz = d + 3 * nc;
+  for (int i = 0; i < s->lat.Q; ++i) {
+    contract_plane_f64<T>(s->nodes[s->f_state[i]], s->n, axis, index, tmp, scr, sb, s->s0);
+    launch_accum_moments<double>(tmp, nc, dr, jx, jy, jz, s->lat.c[i][0], s->lat.c[i][1], s->lat.c[i][2], i == 0, s->s0);
+  }
+  if (s->mask_node >= 0) {
+    if (cudaMalloc(&dm, nc * sizeof(double)) != cudaSuccess) return fin(TNLBM_E_OOM);
+    contract_plane_f64<T>(s->nodes[s->mask_node], s->n, axis, index, dm, scr, sb, s->s0);
+  }
+  if (u) launch_velocity(nc, dr, jx, jy, jz, dm, s->cfg.force[0], s->cfg.force[1], s->cfg.force[2], s->s0);
+  if (rho) cudaMemcpyAsync(rho, dr, nc * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+  if (u) cudaMemcpyAsync(u, jx, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost, s->s0);
+  cudaError_t e = cudaStreamSynchronize(s->s0);
+  if (e != cudaSuccess) return fin(cuda_fail(e, "tnlbm_macroscopic_slice"));
+  return fin(0);
+}
+
+template <typename T>
 static int get_pop_impl(tnlbm_sim* s, double* cores, int* ranks) {
   using namespace tn;
   const size_t ms = mps_size(s->L, s->cfg.chi_max);
@@ -1052,6 +1087,15 @@ extern "C" {
 int tnlbm_macroscopic(tnlbm_sim* s, double* rho, double* u) {
   if (!s) { set_error("sim is NULL"); return TNLBM_E_ARG; }
   return s->prec == TNLBM_FP64 ? macro_impl<double>(s, rho, u) : macro_impl<float>(s, rho, u);
+}
+
+int tnlbm_macroscopic_slice(tnlbm_sim* s, int axis, int index, double* rho, double* u) {
+  if (!s || axis < 0 || axis > 2 || index < 0 || index >= s->N) {
+    set_error("bad arguments to tnlbm_macroscopic_slice");
+    return TNLBM_E_ARG;
+  }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  return s->prec == TNLBM_FP64 ? slice_impl<double>(s, axis, index, rho, u) : slice_impl<float>(s, axis, index, rho, u);
 }
 
 int tnlbm_get_populations(tnlbm_sim* s, double* cores, int* ranks) {
@@ -1095,6 +1139,10 @@ int tnlbm_stats_get(tnlbm_sim* s, tnlbm_stats* out) {
   out->rho0 = scal[SC_RHO0];
   out->status = st;
   out->gpu_launches_per_step = s->launches_per_step;
+  double disc = 0.0;
+  TN_CUDA(cudaMemcpy(&disc, s->d_discard, sizeof(double), cudaMemcpyDeviceToHost));
+  out->discarded2 = disc;
+  out->mass = scal[SC_RHO0] * s->n_fluid;
   out->round_jobs_per_step = 0;
   out->product_jobs_per_step = 0;
   for (auto& lv : s->levels) {

@@ -100,6 +100,11 @@ template <typename T>
 int contract_dense(const MpsRef& X, int n_bits, T* d_dense, void* d_scratch, size_t scratch_bytes,
                    cudaStream_t st);
 size_t contract_scratch_bytes(int n_bits, int cap, size_t elem);
+// plane coordinate[axis] = index of X, out[u * N + v] (the two other axes in order)
+size_t plane_scratch_bytes(int n_bits, int axis, int cap);
+template <typename T>
+int contract_plane_f64(const MpsRef& X, int n_bits, int axis, int index, double* d_plane, void* d_scratch,
+                       size_t scratch_bytes, cudaStream_t st);
 template <typename T>
 int contract_dense_f64(const MpsRef& X, int n_bits, double* d_dense, void* d_scratch, size_t scratch_bytes,
                        cudaStream_t st);

@@ -133,6 +133,7 @@ struct RoundJob {
   const void* masks;          // T*, rank-1 mask table of this job's simulation, or null = launch's
   const double* scal;         // scalars of this job's simulation, or null = launch's
   int L, n_bits;              // chain length and bits per axis of this job, or 0 = launch's
+  double* discard;            // accumulator of squared discarded tails (device), or null
 };
 
 // bound of one term's bond k from the capacities of its operands

@@ -219,6 +219,116 @@ int contract_dense_f64(const MpsRef& X, int n_bits, double* d_dense, void* d_scr
   return contract_dense_to<T, double>(X, n_bits, d_dense, d_scratch, scratch_bytes, st);
 }
 
+// ---------------------------------------------------------------- plane contraction
+// The plane coordinate[axis] = index of an MPS without the N^3 field: the
+// sites of `axis` are fixed to the bits of `index`, the other 2n sites are
+// enumerated as in the dense contraction (prefix rows x suffix columns split
+// at h = L / 2), FP64 accumulation.  Output out[u * N + v], u and v the two
+// remaining coordinates in increasing axis order.
+__host__ __device__ inline int plane_free_bits(int L, int axis, int k0, int k1) {
+  int c = 0;
+  for (int k = k0; k < k1; ++k) c += (k % 3) != axis;
+  return c;
+}
+
+template <typename T>
+__global__ void left_rows_plane_kernel(MpsRef X, int L, int n, int h, int axis, int index, int fp, double* Lm,
+                                       int ldl) {
+  __shared__ double v[1024], w[1024];
+  const size_t l = blockIdx.x;
+  int used = 0;
+  for (int k = 0; k < h; ++k) {
+    int s;
+    if (k % 3 == axis) s = (index >> (n - 1 - k / 3)) & 1;
+    else { s = (int)((l >> (fp - 1 - used)) & 1); ++used; }
+    const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
+    const T* A = (const T*)X.base + core_offset(L, X.cap, k);
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) {
+      double acc = 0.0;
+      if (k == 0) acc = (double)A[(size_t)s * r1 + j];
+      else for (int i = 0; i < r0; ++i) acc += v[i] * (double)A[((size_t)i * 2 + s) * r1 + j];
+      w[j] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < r1; j += blockDim.x) v[j] = w[j];
+    __syncthreads();
+  }
+  const int rh = X.ranks[h];
+  for (int j = threadIdx.x; j < rh; j += blockDim.x) Lm[l * ldl + j] = v[j];
+}
+
+template <typename T>
+__global__ void right_cols_plane_kernel(MpsRef X, int L, int n, int h, int axis, int index, double* Rt, int ldr) {
+  __shared__ double v[1024], w[1024];
+  const size_t q = blockIdx.x;
+  int used = 0;                                    // free sites seen from the right
+  for (int k = L - 1; k >= h; --k) {
+    int s;
+    if (k % 3 == axis) s = (index >> (n - 1 - k / 3)) & 1;
+    else { s = (int)((q >> used) & 1); ++used; }
+    const int r0 = X.ranks[k], r1 = X.ranks[k + 1];
+    const T* A = (const T*)X.base + core_offset(L, X.cap, k);
+    for (int i = threadIdx.x; i < r0; i += blockDim.x) {
+      double acc = 0.0;
+      if (k == L - 1) acc = (double)A[(size_t)i * 2 + s];
+      else for (int j = 0; j < r1; ++j) acc += (double)A[((size_t)i * 2 + s) * r1 + j] * v[j];
+      w[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < r0; i += blockDim.x) v[i] = w[i];
+    __syncthreads();
+  }
+  const int rh = X.ranks[h];
+  for (int j = threadIdx.x; j < rh; j += blockDim.x) Rt[q * ldr + j] = v[j];
+}
+
+__global__ void join_plane_kernel(const int* ranks, int n, int h, int axis, const double* Lm, const double* Rt,
+                                  int ld, double* out) {
+  const int L = 3 * n;
+  const size_t N = (size_t)1 << n;
+  const int rh = ranks[h];
+  const int a0 = axis == 0 ? 1 : 0, a1 = axis == 2 ? 1 : 2;   // remaining axes
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < N * N;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    int c[3] = {0, 0, 0};
+    c[a0] = (int)(idx / N);
+    c[a1] = (int)(idx % N);
+    size_t l = 0, q = 0;
+    for (int k = 0; k < L; ++k) {
+      if (k % 3 == axis) continue;
+      const size_t b = (size_t)((c[k % 3] >> (n - 1 - k / 3)) & 1);
+      if (k < h) l = (l << 1) | b;
+      else q = (q << 1) | b;
+    }
+    const double* pa = Lm + l * ld;
+    const double* pb = Rt + q * ld;
+    double acc = 0.0;
+    for (int j = 0; j < rh; ++j) acc += pa[j] * pb[j];
+    out[idx] = acc;
+  }
+}
+
+size_t plane_scratch_bytes(int n_bits, int axis, int cap) {
+  const int L = 3 * n_bits, h = L / 2;
+  const int fp = plane_free_bits(L, axis, 0, h), fs = plane_free_bits(L, axis, h, L);
+  return (((size_t)1 << fp) + ((size_t)1 << fs)) * (size_t)bond_cap(L, cap, h) * sizeof(double);
+}
+
+template <typename T>
+int contract_plane_f64(const MpsRef& X, int n_bits, int axis, int index, double* d_plane, void* d_scratch,
+                       size_t scratch_bytes, cudaStream_t st) {
+  const int L = 3 * n_bits, h = L / 2;
+  const int ld = bond_cap(L, X.cap, h);
+  if (plane_scratch_bytes(n_bits, axis, X.cap) > scratch_bytes) return TNLBM_E_ARG;
+  const int fp = plane_free_bits(L, axis, 0, h), fs = plane_free_bits(L, axis, h, L);
+  double* Lm = (double*)d_scratch;
+  double* Rt = Lm + ((size_t)1 << fp) * ld;
+  left_rows_plane_kernel<T><<<(unsigned)(1u << fp), 256, 0, st>>>(X, L, n_bits, h, axis, index, fp, Lm, ld);
+  right_cols_plane_kernel<T><<<(unsigned)(1u << fs), 256, 0, st>>>(X, L, n_bits, h, axis, index, Rt, ld);
+  join_plane_kernel<<<152 * 4, 256, 0, st>>>(X.ranks, n_bits, h, axis, Lm, Rt, ld, d_plane);
+  return 0;
+}
+
 template <typename T>
 __global__ void accum_kernel(const T* f, size_t n, double* rho, double* jx, double* jy, double* jz,
                              int cx, int cy, int cz, int first) {
@@ -470,6 +580,7 @@ int tt_svd_dense(const T* d_dense, int n, T* d_dst, int* d_dst_ranks, int dst_ca
 
 #define INST(T)                                                                                   \
   template void launch_inner_ones<T>(const MpsRef*, int, int, double*, cudaStream_t);           \
+  template int contract_plane_f64<T>(const MpsRef&, int, int, int, double*, void*, size_t, cudaStream_t); \
   template void launch_rho0<T>(const MpsRef*, int, double, double*, cudaStream_t);              \
   template void launch_copy<T>(const MpsRef*, const MpsRef*, int, int, cudaStream_t);           \
   template void launch_mass_fix<T>(const MpsRef*, int, int, double*, const double*, cudaStream_t); \

@@ -494,6 +494,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
         const bool cert = sqrt(err2) <= delta || resid2 <= fmax((double)lc->eta * err2, floor2);
         const bool ok = rule_ok && cert && sw < 60 && rr <= bond_cap(L, J.dst.cap, k);
         s_rank = ok ? rr : 0;
+        if (ok && J.discard) atomicAdd(J.discard, err2);
         if (lc->counters) atomicAdd(&lc->counters[ok ? 0 : 1], 1);
         flops += 2.0 * m * n * l * 3 + qr_flops(m, l) + svd_flops(l, n);
       }
@@ -604,6 +605,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
         }
         if (rr > bond_cap(L, J.dst.cap, k)) { s_bad = 1; rr = bond_cap(L, J.dst.cap, k); }
         s_rank = rr;
+        if (J.discard && rr < ncol) atomicAdd(J.discard, s_tau[2 + rr]);   // squared discarded tail
         flops += svd_flops(m, n);
         if (lc && lc->counters) atomicAdd(&lc->counters[2], 1);
       }

@@ -62,6 +62,8 @@ class Stats(ctypes.Structure):
         ("gpu_launches_per_step", ctypes.c_int),
         ("round_jobs_per_step", ctypes.c_int),
         ("product_jobs_per_step", ctypes.c_int),
+        ("mass", ctypes.c_double),
+        ("discarded2", ctypes.c_double),
     ]
 
 
@@ -89,6 +91,8 @@ SIGNATURES = {
     "tnlbm_create": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_void_p)]),
     "tnlbm_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "tnlbm_macroscopic": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tnlbm_macroscopic_slice": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_void_p]),
     "tnlbm_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tnlbm_set_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tnlbm_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),

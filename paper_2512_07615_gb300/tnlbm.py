@@ -406,6 +406,15 @@ class Sim:
         N = self.N
         return rho.reshape(N, N, N), u.reshape(3, N, N, N)
 
+    def macroscopic_slice(self, axis, index):
+        """rho (N, N) and u (3, N, N) on the plane coordinate[axis] = index."""
+        N = self.N
+        rho = np.empty(N * N)
+        u = np.empty(3 * N * N)
+        nat.check(nat.lib().tnlbm_macroscopic_slice(self.h, int(axis), int(index), rho.ctypes.data_as(ctypes.c_void_p),
+                                                    u.ctypes.data_as(ctypes.c_void_p)), "tnlbm_macroscopic_slice")
+        return rho.reshape(N, N), u.reshape(3, N, N)
+
     def get_populations(self):
         ms = mps_size(self.L, self.chi)
         cores = np.empty(self.Q * ms)

@@ -184,3 +184,50 @@ def test_porous_128cubed_bench_configuration_properties(tl):
     solid = sp.astype(bool)
     assert rho[solid].mean() < rho0[solid].mean()
     sim.close()
+
+
+def test_macroscopic_slices_equal_planes_of_the_dense_fields(tl):
+    """tnlbm_macroscopic_slice contracts one plane with the axis's sites fixed:
+    every plane it returns equals that plane of tnlbm_macroscopic (FP32
+    storage, FP64 accumulation in both), for all three axes, with a mask."""
+    n = 4
+    sp = synth.sphere_pack(n, 3.0, 0.3, 5)
+    modes = synth.fourier_modes(9, 2, kmax=3, amp_rho=1e-3, amp_u=1e-2)
+    sim = tl.Sim(n, tau=0.7, periodic=(1, 1, 1), solid=sp, chi_mask=16, eps_mask=1e-8, force=(1e-5, 0, 0),
+                 chi_max=24, eps=1e-7, precision=1, hadamard=0, modes=modes)
+    sim.step(2)
+    rho, u = sim.macroscopic()
+    for axis, index in [(0, 0), (0, 11), (1, 5), (2, 15), (2, 8)]:
+        rs, us = sim.macroscopic_slice(axis, index)
+        sel = [slice(None)] * 3
+        sel[axis] = index
+        np.testing.assert_allclose(rs, rho[tuple(sel)], rtol=0, atol=1e-12)
+        for d in range(3):
+            np.testing.assert_allclose(us[d], u[d][tuple(sel)], rtol=0, atol=1e-12)
+    with pytest.raises(tl.TnlbmError):
+        sim.macroscopic_slice(3, 0)
+    with pytest.raises(tl.TnlbmError):
+        sim.macroscopic_slice(0, 16)
+    sim.close()
+
+
+def test_stats_mass_and_discarded_weight(tl):
+    """stats: `mass` is rho_0 N_fluid from the step's rho_0 node (the lattice
+    sum of rho); `discarded2` accumulates the squared tails cut by every
+    rounding: ~0 without truncation, positive and growing with it."""
+    exact = tl.Sim(3, tau=0.8, periodic=(1, 1, 0), force=(1e-4, 0, 0), chi_max=64, eps=1e-14, precision=0,
+                   hadamard=1, modes=synth.fourier_modes(3, 5, kmax=2, amp_rho=1e-2, amp_u=1e-2))
+    exact.step(2)
+    st = exact.stats()
+    rho, _ = exact.macroscopic()
+    assert abs(st["mass"] - rho.sum()) <= 1e-9 * rho.sum()
+    assert st["discarded2"] <= 1e-20 * rho.sum() ** 2
+    exact.close()
+    trunc = tl.Sim(4, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0, 0), chi_max=8, eps=1e-7, precision=1,
+                   hadamard=0, modes=synth.fourier_modes(15, 1, kmax=3, amp_rho=1e-3, amp_u=1e-2))
+    trunc.step(1)
+    d1 = trunc.stats()["discarded2"]
+    trunc.step(1)
+    d2 = trunc.stats()["discarded2"]
+    assert 0 < d1 < d2
+    trunc.close()
