@@ -24,7 +24,8 @@
  *     tnlbm_mps_offset(L, cap, k); inside the slot the core is packed
  *     [r_k][2][r_(k+1)] row-major with its realised bonds r.  Realised bonds
  *     are an int32 array r[0..L] with r[0] = r[L] = 1.
- *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32 buffers float.
+ *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32 and TNLBM_TF32
+ *     buffers float.
  *   - stream arguments are cudaStream_t values passed as void* (NULL = legacy
  *     default stream).  Primitive calls are asynchronous on that stream unless
  *     stated; they allocate their own scratch with cudaMalloc and free it
@@ -51,7 +52,7 @@ enum {
   TNLBM_E_CAPACITY = -7  /* a realised bond exceeded a buffer capacity   */
 };
 
-enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1 };
+enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2 };
 enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
 enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1, TNLBM_HADAMARD_ZIPUP = 2 };
 
@@ -78,7 +79,9 @@ typedef struct {
   int chi_max;             /* bond cap chi of every rounding (Sec. 2.1)        */
   double eps;              /* relative rounding tolerance: keep the smallest
                               rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
-  int precision;           /* TNLBM_FP64 or TNLBM_FP32                         */
+  int precision;           /* TNLBM_FP64, TNLBM_FP32, or TNLBM_TF32 (FP32
+                              storage; the fit's core contractions on the
+                              tensor cores with TF32 operands, FP32 sums)      */
   int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default), _EXACT
                               (Eq. mul followed by a rounding) or _ZIPUP (the
                               zip-up pass, then a rounding; chi_max <= 512)     */
@@ -270,7 +273,8 @@ int tnlbm_hadamard_zipup(int precision, int n_bits, int batch,
 
 /* A[b] ~ B[b] . C[b] by the single-site variational fit of Sec. 2.3: candidate
  * A = B (bonds unchanged), `sweeps` round trips of local updates and QR/LQ
- * centre shifts.  A must have capacity >= B's. */
+ * centre shifts.  A must have capacity >= B's.  precision TNLBM_TF32: float
+ * buffers, the contractions on the tensor cores (TF32 operands). */
 int tnlbm_hadamard_fit(int precision, int n_bits, int batch,
                        const void *const *B, const int *const *rB, int capB,
                        const void *const *C, const int *const *rC, int capC,

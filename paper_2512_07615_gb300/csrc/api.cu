@@ -572,7 +572,8 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
       cudaStreamWaitEvent(s->s1, s->ev_fork, 0);
     }
     if (!lv.fj.empty())
-      n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof);
+      n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof,
+                      s->prec == TNLBM_TF32);
     if (!lv.zj.empty()) {
       n += run_zipup<T>(lv.d_zj, (int)lv.zj.size(), s->L, s->d_status, both ? s->s1 : s->s0, ctr);
       if (prof) prof->mark(C_ZIPUP);
@@ -930,7 +931,10 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (!(C.tau > 0.5)) { set_error("tau must exceed 0.5"); return TNLBM_E_ARG; }
   if (C.chi_max < 1 || C.chi_max > 512) { set_error("chi_max must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.eps < 0.0) { set_error("eps must be >= 0"); return TNLBM_E_ARG; }
-  if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32) { set_error("bad precision"); return TNLBM_E_ARG; }
+  if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32 && C.precision != TNLBM_TF32) {
+    set_error("bad precision");
+    return TNLBM_E_ARG;
+  }
   if (C.hadamard != TNLBM_HADAMARD_FIT && C.hadamard != TNLBM_HADAMARD_EXACT && C.hadamard != TNLBM_HADAMARD_ZIPUP) {
     set_error("bad hadamard mode");
     return TNLBM_E_ARG;
@@ -1366,7 +1370,7 @@ static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* ter
 }
 
 template <typename T>
-static int fit_impl(int n_bits, int batch, const void* const* B, const int* const* rB, int capB,
+static int fit_impl(int n_bits, int batch, bool tc, const void* const* B, const int* const* rB, int capB,
                     const void* const* C, const int* const* rC, int capC, void* const* A,
                     int* const* rA, int capA, int sweeps, cudaStream_t st) {
   const int L = 3 * n_bits;
@@ -1403,7 +1407,7 @@ static int fit_impl(int n_bits, int batch, const void* const* B, const int* cons
   }
   TN_CUDA(cudaMemcpyAsync(dj.p, jobs.data(), batch * sizeof(FitJob), cudaMemcpyHostToDevice, st));
   TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
-  run_fit<T>((const FitJob*)dj.p, jobs, L, sweeps, (int*)ds.p, st);
+  run_fit<T>((const FitJob*)dj.p, jobs, L, sweeps, (int*)ds.p, st, nullptr, tc);
   TN_CUDA(cudaGetLastError());
   return check_status((int*)ds.p, st);
 }
@@ -1543,8 +1547,9 @@ int tnlbm_hadamard_fit(int precision, int n_bits, int batch, const void* const* 
   if (batch == 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
   return precision == TNLBM_FP64
-             ? tn::fit_impl<double>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st)
-             : tn::fit_impl<float>(n_bits, batch, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st);
+             ? tn::fit_impl<double>(n_bits, batch, false, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st)
+             : tn::fit_impl<float>(n_bits, batch, precision == TNLBM_TF32, B, rB, capB, C, rC, capC, A, rA, capA,
+                                   sweeps, st);
 }
 
 int tnlbm_inner_ones(int precision, int n_bits, int batch, const void* const* X, const int* const* rX,
@@ -1727,7 +1732,9 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
         if (!lv.fg[gi].fj.empty() || !lv.fg[gi].zj.empty()) cudaStreamWaitEvent(b->sfit[gi], b->ev_fork, 0);
       for (int gi = 0; gi < ng; ++gi) {
         auto& g = lv.fg[gi];
-        if (!g.fj.empty()) nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr);
+        if (!g.fj.empty())
+          nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr,
+                           b->prec == TNLBM_TF32);
         if (!g.zj.empty())
           nl += run_zipup<T>(g.d_zj, (int)g.zj.size(), b->lens[gi], b->d_status, b->sfit[gi], nullptr);
       }

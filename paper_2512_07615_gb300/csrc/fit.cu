@@ -15,6 +15,7 @@
 
 #include "fit.cuh"
 #include "gemm.cuh"
+#include "tcgemm.cuh"
 #include "linalg.cuh"
 
 namespace tn {
@@ -136,6 +137,32 @@ __global__ void __launch_bounds__(G_THREADS) fit_gemm_kernel(const FitJob* __res
   const int k0 = imin(d.K, split * kc), k1 = imin(d.K, k0 + kc);
   T* part = (T*)J.x + ((size_t)split * nb + ib) * d.M * d.N;
   gemm_tile<T>(d, blockIdx.x, ib, k0, k1, part);
+}
+
+// fit_gemm_kernel<float, STAGE> with the tiles on the tensor cores (TF32
+// operands, FP32 accumulation; same grid, split-K ranges and outputs).
+template <int STAGE>
+__global__ void __launch_bounds__(G_THREADS) fit_gemm_tc_kernel(const FitJob* __restrict__ jobs, int L, int c,
+                                                                double* ctr, int splits, int nbm, int* status) {
+  const FitJob& J = jobs[blockIdx.z];
+  RankSrc R{&J, false, L};
+  GDesc d = make_desc<float>(STAGE, J, c, R);
+  if (ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    atomicAdd(&ctr[C_FIT_GEMM], 2.0 * d.M * d.N * d.K * d.nb_hi * d.nb_lo);
+  if (splits <= 1) {
+    gemm_tile_tc(d, blockIdx.x, blockIdx.y, 0, d.K, nullptr, status);
+    return;
+  }
+  const int split = blockIdx.y / nbm, ib = blockIdx.y % nbm;
+  const int nb = d.nb_hi * d.nb_lo;
+  RankSrc Rc{&J, true, L};
+  const int sj = job_splits(make_desc<float>(STAGE, J, c, Rc).K);
+  if (ib >= nb || split >= sj) return;
+  splits = sj;
+  const int kc = ((d.K + splits - 1) / splits + GB_K - 1) / GB_K * GB_K;
+  const int k0 = imin(d.K, split * kc), k1 = imin(d.K, k0 + kc);
+  float* part = (float*)J.x + ((size_t)split * nb + ib) * d.M * d.N;
+  gemm_tile_tc(d, blockIdx.x, ib, k0, k1, part, status);
 }
 
 template <typename T, int STAGE>
@@ -295,7 +322,7 @@ static void set_fit_smem() {
 // ---------------------------------------------------------------- host driver
 template <typename T, int STAGE>
 static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int c,
-                        cudaStream_t st, Prof* prof) {
+                        cudaStream_t st, Prof* prof, bool tc, int* d_status) {
   int tiles = 1, nb = 1, kmax = 1;
   size_t elems = 1;
   for (const FitJob& j : hj) {
@@ -312,7 +339,16 @@ static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int
   int splits = 1;
   if (STAGE == S3 || STAGE == T3) splits = job_splits(kmax);
   dim3 grid(tiles, nb * splits, (unsigned)hj.size());
-  fit_gemm_kernel<T, STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr, splits, nb);
+  bool launched = false;
+  if constexpr (sizeof(T) == 4) {
+    if (tc) {
+      fit_gemm_tc_kernel<STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr, splits, nb,
+                                                            d_status);
+      launched = true;
+    }
+  }
+  if (!launched)
+    fit_gemm_kernel<T, STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr, splits, nb);
   if (splits > 1) {
     const unsigned rb = (unsigned)std::min<size_t>(64, (elems + 255) / 256);
     fit_splitk_reduce<T, STAGE><<<dim3(rb, (unsigned)hj.size()), 256, 0, st>>>(d_jobs, L, c, splits);
@@ -323,7 +359,7 @@ static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int
 
 template <typename T>
 int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int sweeps,
-            int* d_status, cudaStream_t st, Prof* prof) {
+            int* d_status, cudaStream_t st, Prof* prof, bool tc) {
   const int nj = (int)hj.size();
   if (nj == 0) return 0;
   double* ctr = prof ? prof->d_ctr : nullptr;
@@ -334,18 +370,18 @@ int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int swee
   rortho_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, d_status, ctr); ++launches; mark(C_FIT_QR);
   env_edges_kernel<T><<<nj, 32, 0, st>>>(d_jobs, L); ++launches; mark(C_FIT_MISC);
   for (int c = L - 1; c >= 1; --c) {
-    launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
-    launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
-    launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
+    launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof, tc, d_status);
+    launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof, tc, d_status);
+    launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof, tc, d_status);
   }
   for (int sw = 0; sw < sweeps; ++sw) {
     for (int c = 0; c < L; ++c) {
-      launches += launch_stage<T, S1>(d_jobs, hj, L, c, st, prof);
-      launches += launch_stage<T, S2>(d_jobs, hj, L, c, st, prof);
-      launches += launch_stage<T, S3>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, S1>(d_jobs, hj, L, c, st, prof, tc, d_status);
+      launches += launch_stage<T, S2>(d_jobs, hj, L, c, st, prof, tc, d_status);
+      launches += launch_stage<T, S3>(d_jobs, hj, L, c, st, prof, tc, d_status);
       if (c < L - 1) {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 0, d_status, ctr); mark(C_FIT_QR);
-        launches += launch_stage<T, ENVR>(d_jobs, hj, L, c, st, prof);
+        launches += launch_stage<T, ENVR>(d_jobs, hj, L, c, st, prof, tc, d_status);
         launches += 1;
       } else {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 2, d_status, ctr); mark(C_FIT_MISC);
@@ -353,12 +389,12 @@ int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int swee
       }
     }
     for (int c = L - 1; c >= 0; --c) {
-      launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof);
-      launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof);
-      launches += launch_stage<T, T3>(d_jobs, hj, L, c, st, prof);
+      launches += launch_stage<T, T1>(d_jobs, hj, L, c, st, prof, tc, d_status);
+      launches += launch_stage<T, T2>(d_jobs, hj, L, c, st, prof, tc, d_status);
+      launches += launch_stage<T, T3>(d_jobs, hj, L, c, st, prof, tc, d_status);
       if (c > 0) {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 1, d_status, ctr); mark(C_FIT_QR);
-        launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof);
+        launches += launch_stage<T, ENVL>(d_jobs, hj, L, c, st, prof, tc, d_status);
         launches += 1;
       } else {
         shift_centre_kernel<T><<<nj, FT, FIT_SMEM, st>>>(d_jobs, L, c, 2, d_status, ctr); mark(C_FIT_MISC);
@@ -398,7 +434,7 @@ void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* 
   *q_elems = (q + 31) & ~(size_t)31;
 }
 
-template int run_fit<float>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*);
-template int run_fit<double>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*);
+template int run_fit<float>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, bool);
+template int run_fit<double>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, bool);
 
 }  // namespace tn

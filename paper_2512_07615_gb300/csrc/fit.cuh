@@ -67,9 +67,10 @@ struct Prof {
   }
 };
 
+// tc: the GEMM stages on the tensor cores (tcgen05 kind::tf32; float storage only)
 template <typename T>
 int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int sweeps, int* d_status,
-            cudaStream_t st, Prof* prof = nullptr);
+            cudaStream_t st, Prof* prof = nullptr, bool tc = false);
 
 // ---- misc.cu
 // out[b] = <X_b, 1> for MPS refs in device memory
