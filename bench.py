@@ -78,7 +78,7 @@ def make_sim(w, solid, modes):
     return tl.Sim(w["n"], lattice=w["lattice"], tau=w["tau"], periodic=w["periodic"], solid=solid,
                   chi_mask=w["chi_mask"], eps_mask=w["eps_mask"], force=w["force"], chi_max=w["chi"],
                   eps=w["eps"], precision=w["precision"], hadamard=0, sweeps=2, modes=modes,
-                  conserve_mass=w["precision"] == 1)
+                  conserve_mass=w["precision"] != 0)
 
 
 class Clocks:
@@ -344,10 +344,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "tf32"], default=None,
+                    help="override the workload's precision (tf32: FP32 storage, fit contractions on the "
+                         "tensor cores with TF32 operands)")
     ap.add_argument("--batched-mixed", action="store_true",
                     help="also time the eight uneven simulations (64^3-256^3, chi 32-128) in one graph")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.precision:
+        w["precision"] = {"fp64": 0, "fp32": 1, "tf32": 2}[args.precision]
     N3 = float((1 << w["n"]) ** 3)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -364,8 +369,10 @@ def main():
     config = {"workload": args.workload, "lattice": "D3Q%d" % w["lattice"], "cells": "%d^3" % (1 << w["n"]),
               "chi_max": w["chi"], "chi_mask": w["chi_mask"] if solid is not None else None,
               "eps": w["eps"], "tau": w["tau"], "products": "variational fit, 2 sweeps",
-              "storage": "fp32" if w["precision"] == 1 else "fp64",
-              "mass_correction": w["precision"] == 1,
+              "storage": "fp64" if w["precision"] == 0 else "fp32",
+              "contractions": {0: "fp64 SIMT", 1: "fp32 SIMT", 2: "tf32 tensor cores (fit), fp32 SIMT (rounding)"}[
+                  w["precision"]],
+              "mass_correction": w["precision"] != 0,
               "start": ("Taylor-Green vortex u0 = %g" % w["tgv_u0"]) if w.get("tgv_u0") else
                        ("%d seeded Fourier modes" % w["n_modes"] if w["n_modes"] else "rest"),
               "l2_flush": "working set > L2 (129 MB) is not claimed; each step touches ~GBs of environments"}
@@ -433,7 +440,7 @@ def main():
     total_prof_ms = sum(v["ms"] for v in prof.values())
     dom = max(prof, key=lambda c: prof[c]["ms"])
     peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
-    fp32 = w["precision"] == 1
+    fp32 = w["precision"] != 0
     if fp32:
         peak_tf, peak_src = FP32_SIMT_MEASURED_TFLOPS, "measured FP32 SIMT SGEMM on this pool (no TF32)"
     else:
@@ -462,6 +469,14 @@ def main():
                                       ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")), 1.0), 4)
                                       for p in ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")},
                 "jacobi_sweeps_per_svd": round_phases["jacobi_sweeps"] / max(round_phases["svd_count"], 1.0)}
+    if w["precision"] == 2 and prof["fit_gemm"]["ms"] > 0:
+        # the fit's GEMM stages on the tensor cores: against the TF32 peak, taken
+        # as the measured BF16 burst peak times the nominal TF32 / BF16 ratio
+        tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        ach_tc = prof["fit_gemm"]["flops"] / (prof["fit_gemm"]["ms"] / 1e3) / 1e12
+        roofline["tensor"] = {"kernel": "fit_gemm_tc", "bound": "tensor", "achieved": ach_tc, "peak": tf32_peak,
+                              "unit": "TFLOP/s", "frac": ach_tc / tf32_peak,
+                              "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
 
     # end to end through the C ABI: populations host -> device, step, device -> host
     e2e = None
@@ -498,7 +513,7 @@ def main():
         out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f32" if fp32 else "f64", "data": "synthetic", "config": config,
+               "dtype": ("tf32" if w["precision"] == 2 else "f32") if fp32 else "f64", "data": "synthetic", "config": config,
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
