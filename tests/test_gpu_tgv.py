@@ -66,3 +66,29 @@ def test_tgv_production_path_fp32(tl):
     assert abs(e - e_d) / e_d <= 1e-3
     assert abs(rho.sum() - rho0.sum()) / rho0.sum() <= 1e-6        # drift of its own mass
     sim.close()
+
+
+def test_tgv_fp64_near_half_tau_tracks_dense_energy(tl):
+    """Near tau = 1/2 (tau = 0.5038, omega ~ 1.985) the FP64 path keeps the
+    dense oracle's kinetic-energy history (16^3, chi 32, eps 1e-10, 100
+    steps): E/E0 at every 25 steps within 1e-6."""
+    n, tau, u0, steps = 4, 0.5038, 0.05, 100
+    sim = tl.Sim(n, tau=tau, periodic=(1, 1, 1), chi_max=32, eps=1e-10, precision=0, hadamard=0,
+                 modes=synth.taylor_green_modes(u0))
+    lat = lattice.D3Q19
+    cfg = ml.Config(n, lat, tau, chi_max=64, eps=0.0)
+    fd = ml.to_dense_populations(ml.initial_perturbed(cfg, synth.taylor_green_modes(u0)))
+    e_mps, e_dense = [], []
+    for t in range(0, steps + 1, 25):
+        if t:
+            sim.step(25)
+            for _ in range(25):
+                fd = ld.step(fd, lat, tau, (0.0, 0.0, 0.0), None, (1, 1, 1), "taylor")
+        rho, u = sim.macroscopic()
+        e_mps.append(0.5 * float(np.sum(rho * np.sum(u ** 2, axis=0))))
+        rd, ud = ld.velocity_out(lat, fd)
+        e_dense.append(0.5 * float(np.sum(rd * np.sum(ud ** 2, axis=0))))
+    for a, b in zip(e_mps, e_dense):
+        assert abs(a / e_mps[0] - b / e_dense[0]) <= 1e-6
+    assert e_dense[-1] < e_dense[0]
+    sim.close()
