@@ -81,7 +81,10 @@ typedef struct {
                               rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
   int precision;           /* TNLBM_FP64, TNLBM_FP32, or TNLBM_TF32 (FP32
                               storage; the fit's core contractions on the
-                              tensor cores with TF32 operands, FP32 sums)      */
+                              tensor cores with TF32 operands, FP32 sums).
+                              Near tau = 1/2 (weakly damped flows) the FP32
+                              one-sided Jacobi of the roundings leaves errors
+                              the collision does not damp: use TNLBM_FP64  */
   int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default), _EXACT
                               (Eq. mul followed by a rounding) or _ZIPUP (the
                               zip-up pass, then a rounding; chi_max <= 512)     */

@@ -54,84 +54,6 @@ __device__ inline double block_sum(double v, double* red) {
   return s;
 }
 
-// Householder QR of A (m x n, leading dim lda), in place: on return the upper
-// triangle holds R and the strict lower part the reflector tails.  tau[k],
-// k = min(m, n), receives the reflector scalars (H = I - tau v v^T, v_0 = 1).
-// Then Q (m x k, ld = k) is formed explicitly and R (k x n, ld = n) is copied
-// out with rows sign-normalised so that diag(R) >= 0.
-template <typename T>
-__device__ void householder_qr(T* A, int m, int n, int lda, T* Q, T* R, double* tau,
-                               double* red) {
-  const int kk = imin(m, n);
-  for (int j = 0; j < kk; ++j) {
-    double part = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
-      double v = (double)A[(size_t)i * lda + j];
-      part += v * v;
-    }
-    double sig2 = block_sum(part, red);
-    __shared__ double s_scale;
-    if (threadIdx.x == 0) {
-      double alpha = (double)A[(size_t)j * lda + j];
-      if (sig2 == 0.0) {
-        tau[j] = 0.0;
-        s_scale = 0.0;
-      } else {
-        double beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
-        tau[j] = (beta - alpha) / beta;
-        s_scale = 1.0 / (alpha - beta);
-        A[(size_t)j * lda + j] = (T)beta;
-      }
-    }
-    __syncthreads();
-    const double tj = tau[j];
-    if (tj != 0.0) {
-      const double sc = s_scale;
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x)
-        A[(size_t)i * lda + j] = (T)((double)A[(size_t)i * lda + j] * sc);
-      __syncthreads();
-      for (int c = j + 1 + threadIdx.x; c < n; c += blockDim.x) {
-        T w = A[(size_t)j * lda + c];
-        for (int i = j + 1; i < m; ++i) w += A[(size_t)i * lda + j] * A[(size_t)i * lda + c];
-        w *= (T)tj;
-        A[(size_t)j * lda + c] -= w;
-        for (int i = j + 1; i < m; ++i) A[(size_t)i * lda + c] -= w * A[(size_t)i * lda + j];
-      }
-    }
-    __syncthreads();
-  }
-  // R with non-negative diagonal; remember the signs in tau's sign? keep separate
-  for (int idx = threadIdx.x; idx < kk * n; idx += blockDim.x) {
-    int i = idx / n, c = idx % n;
-    T d = A[(size_t)i * lda + i] < (T)0 ? (T)-1 : (T)1;
-    R[(size_t)i * n + c] = c >= i ? d * A[(size_t)i * lda + c] : (T)0;
-  }
-  // Q = H_0 ... H_{kk-1} [I; 0], accumulated backwards
-  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
-    int i = idx / kk, c = idx % kk;
-    Q[idx] = (i == c) ? (T)1 : (T)0;
-  }
-  __syncthreads();
-  for (int j = kk - 1; j >= 0; --j) {
-    const double tj = tau[j];
-    if (tj != 0.0) {
-      for (int c = j + threadIdx.x; c < kk; c += blockDim.x) {
-        T w = Q[(size_t)j * kk + c];
-        for (int i = j + 1; i < m; ++i) w += A[(size_t)i * lda + j] * Q[(size_t)i * kk + c];
-        w *= (T)tj;
-        Q[(size_t)j * kk + c] -= w;
-        for (int i = j + 1; i < m; ++i) Q[(size_t)i * kk + c] -= w * A[(size_t)i * lda + j];
-      }
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < m * kk; idx += blockDim.x) {
-    int c = idx % kk;
-    if (A[(size_t)c * lda + c] < (T)0) Q[idx] = -Q[idx];
-  }
-  __syncthreads();
-}
-
 // One-sided Jacobi on ncol columns of length len, stored column-contiguous
 // (Wm[j*len + i]); V (ncol x ncol, V[j*ncol + i] = column j) accumulates the
 // rotations.  Parallel ordering: a round-robin tournament, one warp per pair.
@@ -488,94 +410,6 @@ template <> __device__ __forceinline__ void v_rot<double>(double2& x, double2& y
   const double2 a = x, b = y;
   x = make_double2(c * a.x - s * b.x, c * a.y - s * b.y);
   y = make_double2(s * a.x + c * b.x, s * a.y + c * b.y);
-}
-
-// One-sided Jacobi (same pair order, tolerance and rotation as jacobi_cols_hw)
-// with a warp per column pair: each column is read once as 16-byte vectors,
-// rotated in registers and written once, so that the shared-memory traffic is
-// one read and one write per column and pair, without bank conflicts.
-// Requires ldw and ldv to be multiples of 16 / sizeof(T) elements, Wm and V
-// 16-byte aligned and len <= 32 * NV * (16 / sizeof(T)).  Column entries
-// [len, round_up(len, 16 / sizeof(T))) are zeroed here, V is set to I.
-template <typename T, int NV>
-__device__ __noinline__ int jacobi_cols_w(T* Wm, int ldw, T* V, int ldv, int ncol, int len, int maxsw) {
-  typedef typename Vec16<T>::t VT;
-  constexpr int VW = Vec16<T>::n;
-  const int lenv = (len + VW - 1) / VW, ncv = (ncol + VW - 1) / VW;
-  const int padw = lenv * VW - len;
-  for (int idx = threadIdx.x; idx < ncol * padw; idx += blockDim.x)
-    Wm[(size_t)(idx / padw) * ldw + len + idx % padw] = (T)0;
-  for (int idx = threadIdx.x; idx < ncol * ncv * VW; idx += blockDim.x) {
-    const int r = idx / (ncv * VW), c = idx % (ncv * VW);
-    V[(size_t)r * ldv + c] = (r == c) ? (T)1 : (T)0;
-  }
-  __shared__ int s_rot;
-  __syncthreads();
-  if (ncol < 2) return 0;
-  const int np = (ncol + 1) & ~1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const T tolT = (T)(16.0 * Eps<T>::v * sqrt((double)len));
-  const T floor2 = sizeof(T) == 8 ? (T)1e-250 : (T)1e-24;
-  int sweep = 0;
-  for (; sweep < maxsw; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int p = warp; p < np / 2; p += nw) {
-        int a, b;
-        if (p == 0) { a = rnd; b = np - 1; }
-        else { a = (rnd + p) % (np - 1); b = (rnd - p + (np - 1)) % (np - 1); }
-        if (a > b) { int t = a; a = b; b = t; }
-        if (b >= ncol) continue;                       // the dummy column of an odd count
-        VT* pa = (VT*)(Wm + (size_t)a * ldw);
-        VT* pb = (VT*)(Wm + (size_t)b * ldw);
-        VT xa[NV], xb[NV];
-        T al = (T)0, be = (T)0, ga = (T)0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const int i = lane + 32 * v;
-          if (i < lenv) {
-            xa[v] = pa[i];
-            xb[v] = pb[i];
-            v_dot3<T>(xa[v], xb[v], al, be, ga);
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        if (ga == (T)0 || al < floor2 || be < floor2 || fabs(ga) <= tolT * sqrt(al) * sqrt(be)) continue;
-        const T zeta = (be - al) / ((T)2 * ga);
-        const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + hypot((T)1, zeta));
-        const T cc = (T)1 / sqrt((T)1 + t * t), ss = cc * t;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const int i = lane + 32 * v;
-          if (i < lenv) {
-            v_rot<T>(xa[v], xb[v], cc, ss);
-            pa[i] = xa[v];
-            pb[i] = xb[v];
-          }
-        }
-        VT* va = (VT*)(V + (size_t)a * ldv);
-        VT* vb = (VT*)(V + (size_t)b * ldv);
-        for (int i = lane; i < ncv; i += 32) {
-          VT x = va[i], y = vb[i];
-          v_rot<T>(x, y, cc, ss);
-          va[i] = x;
-          vb[i] = y;
-        }
-        if (lane == 0) s_rot = 1;
-      }
-      __syncthreads();
-    }
-    const int any = s_rot;
-    __syncthreads();
-    if (!any) break;
-  }
-  return sweep;
 }
 
 // Row stride of a Jacobi matrix for jacobi_cols_fast (16-byte multiple).
