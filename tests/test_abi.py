@@ -76,3 +76,41 @@ def test_oracle_not_imported_by_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("no oracle", ""), f
+
+
+def test_argument_errors_of_the_newer_entry_points(lib):
+    """Zip-up product, plane slices, batches and the config options added
+    with them (precision TF32, zip-up products, block sums) reject bad
+    arguments before any device call."""
+    import paper_2512_07615_gb300.native as nat
+    h = ctypes.c_void_p()
+    # zip-up primitive: NULL operands, chi above the supported 512
+    assert lib.tnlbm_hadamard_zipup(0, 3, 1, None, None, 4, None, None, 4, None, None, 8, 8, 0.0, None) == -1
+    assert b"zipup" in lib.tnlbm_last_error()
+    assert lib.tnlbm_hadamard_zipup(0, 3, 0, None, None, 4, None, None, 4, None, None, 600, 600, 0.0, None) == -1
+    # plane slice of no simulation
+    assert lib.tnlbm_macroscopic_slice(None, 0, 0, None, None) == -1
+    # batches
+    assert lib.tnlbm_batch_create(None, 0, ctypes.byref(h)) == -1
+    assert lib.tnlbm_batch_step(None, 1) == -1
+    c = nat.Config()
+    c.n_per_axis = 3
+    c.lattice = 19
+    c.tau = 0.8
+    c.chi_max = 8
+    c.eps = 1e-8
+    c.precision = 3                     # no such precision
+    assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"precision" in lib.tnlbm_last_error()
+    c.precision = nat.TF32
+    c.hadamard = 3                      # no such product
+    assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"hadamard" in lib.tnlbm_last_error()
+    c.hadamard = nat.HADAMARD_ZIPUP
+    c.chi_max = 600                     # zip-up bonds are capped at 512
+    assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    c.hadamard = nat.HADAMARD_FIT
+    c.chi_max = 64
+    c.block_sums = 1                    # 19 x 64 > 1024: the summed bond of one rounding
+    assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"block_sums" in lib.tnlbm_last_error()
