@@ -98,3 +98,27 @@ def test_inlet_outlet_fp32_tracks_dense(tl):
     assert np.abs(rho - rho_d).max() <= 1e-4
     assert sim.stats()["status"] == 0
     sim.close()
+
+
+def test_step_options_combined_equal_dense(tl):
+    """Zip-up products, block-sum moments, inlet / outlet faces with walls,
+    an object mask (the oracle's TT-SVD cores) and a body force together,
+    FP64, nothing truncated (8^3: chi 48 holds every bond): one step equals
+    the dense step."""
+    from oracle import mps as M, quantics as q
+    n, tau = 3, 0.8
+    box = synth.box_obstacle(n, (3, 2, 2), (5, 5, 4)).astype(float)
+    mask = M.tt_svd(q.encode(box), 10 ** 6, 1e-14)
+    spec = {0: (V, (0.02, 0.0, 0.01), 1.0), 1: (P, (0.0, 0.0, 0.0), 0.999)}
+    modes = synth.fourier_modes(3, 9, kmax=2, amp_rho=1e-2, amp_u=1e-2)
+    sim = tl.Sim(n, tau=tau, periodic=(0, 1, 0), mask_cores=mask, force=(1e-4, 0.0, 0.0), chi_max=48, eps=1e-14,
+                 precision=0, hadamard=2, block_sums=True, modes=modes, faces=spec)
+    fd = start(n, modes)
+    sim.step(1)
+    fd = ld.step(fd, lattice.D3Q19, tau, (1e-4, 0.0, 0.0), box, (0, 1, 0), "taylor", faces=dense_faces(spec))
+    rho, u = sim.macroscopic()
+    rho_d, u_d = ld.velocity_out(lattice.D3Q19, fd, (1e-4, 0.0, 0.0), box)
+    assert rel_l2(u, u_d) <= 1e-10
+    assert np.abs(rho - rho_d).max() <= 1e-12
+    assert sim.stats()["status"] == 0
+    sim.close()

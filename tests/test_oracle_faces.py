@@ -62,3 +62,21 @@ def test_mps_faces_equal_dense_untruncated():
     assert np.abs(fw - ld.step(ml.to_dense_populations(ml.initial_perturbed(cfg, modes)), lat, 0.8, (0, 0, 0),
                                None, (0, 1, 0), "taylor", faces=faces)).max() > 1e-4
 
+
+
+def test_mps_options_combined_equal_dense_untruncated():
+    """The step options together -- zip-up products, block-sum moments, an
+    inlet and an outlet with walls, an object mask and a body force -- still
+    reproduce the dense step when nothing is truncated (8^3, one step)."""
+    from oracle import mps as M, quantics as q
+    lat = lattice.D3Q19
+    box = synth.box_obstacle(3, (3, 2, 2), (5, 5, 4)).astype(float)
+    mask = M.tt_svd(q.encode(box), 10 ** 6, 1e-14)
+    faces = faces_of({0: (V, (0.02, 0.0, 0.01), 1.0), 1: (P, (0.0, 0.0, 0.0), 0.999)})
+    cfg = ml.Config(3, lat, 0.8, force=(1e-4, 0.0, 0.0), periodic=(0, 1, 0), chi_max=10 ** 6, eps=0.0,
+                    hadamard="zipup", block_sums=True, mask=mask, faces=faces)
+    f = ml.initial_perturbed(cfg, synth.fourier_modes(3, 9, kmax=2, amp_rho=1e-2, amp_u=1e-2))
+    fd = ml.to_dense_populations(f)
+    f = ml.step(cfg, f)
+    fd = ld.step(fd, lat, 0.8, (1e-4, 0.0, 0.0), box, (0, 1, 0), "taylor", faces=faces)
+    assert np.abs(ml.to_dense_populations(f) - fd).max() <= 1e-12 * np.abs(fd).max()
