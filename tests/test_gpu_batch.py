@@ -99,3 +99,31 @@ def test_batch_rejects_mixed_precision(tl):
     cfgs[1] = dict(cfgs[1], precision=0)
     with pytest.raises(tl.nat.TnlbmError):
         tl.Batch(cfgs)
+
+
+@pytest.mark.parametrize("precision,hadamard", [(1, 2), (2, 0)])
+def test_batch_with_zipup_or_tensor_core_products_equals_alone(tl, precision, hadamard):
+    """Batches whose products are zip-up passes (their own stream per chain
+    length) or tensor-core fits (TF32): bitwise the simulations alone, for
+    two lattice sizes."""
+    cfgs = [
+        dict(n_per_axis=3, tau=0.8, periodic=(1, 1, 0), force=(1e-5, 0, 0), chi_max=8, eps=1e-7,
+             precision=precision, hadamard=hadamard,
+             modes=synth.fourier_modes(2, 1, kmax=1, amp_rho=1e-3, amp_u=1e-2)),
+        dict(n_per_axis=4, tau=0.7, periodic=(1, 1, 1), solid=synth.sphere_pack(4, 2.0, 0.25, 2), chi_mask=16,
+             eps_mask=1e-8, force=(1e-5, 0, 0), chi_max=16, eps=1e-7, precision=precision, hadamard=hadamard,
+             modes=synth.fourier_modes(7, 3, kmax=2, amp_rho=1e-3, amp_u=1e-3)),
+    ]
+    b = tl.Batch(cfgs)
+    b.step(2)
+    got = [s.macroscopic() for s in b.sims]
+    for i, kw in enumerate(cfgs):
+        kw = dict(kw)
+        n = kw.pop("n_per_axis")
+        alone = tl.Sim(n, **kw)
+        alone.step(2)
+        rho, u = alone.macroscopic()
+        alone.close()
+        assert np.array_equal(rho, got[i][0]) and np.array_equal(u, got[i][1]), i
+        assert b.sims[i].stats()["status"] == 0
+    b.close()
