@@ -100,3 +100,16 @@ def test_tf32_step_vs_fp64_dense(tl):
     assert abs(rho.sum() - rho_start.sum()) / rho_start.sum() <= 1e-6
     assert sim.stats()["status"] == 0
     sim.close()
+
+
+def test_tf32_fit_with_split_k_tracks_fp32(tl):
+    """Bonds 32 x 16 (K = g b = 512 in the S3 / T3 stages: split-K partial
+    tiles written by the tensor-core kernel and summed in order): the TF32
+    fit stays within 3e-3 of the FP32 fit."""
+    n = 5
+    B = M.tt_svd(q.encode(smooth(n, 5, n_modes=16)), 32, 0.0)
+    C = M.tt_svd(q.encode(smooth(n, 6, n_modes=6)), 16, 0.0)
+    a32 = _fit(tl, B, C, 32, 1)
+    a_tc = _fit(tl, B, C, 32, 2)
+    assert max(x.shape[2] for x in B) == 32 and max(x.shape[2] for x in C) >= 16
+    assert rel(M.to_tensor(a_tc), M.to_tensor(a32)) < 3e-3
