@@ -53,6 +53,11 @@ WORKLOADS = {
     "vessel256": dict(n=8, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
                       chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=1, geometry="vessel",
                       radius=24.0, depth=4, geo_seed=0, n_modes=31, mode_seed=0),
+    # the vessel's per-job shapes (chi 128: 256-wide centre matrices, Jacobi in
+    # global memory) on 64^3, for kernel captures
+    "vessel64": dict(n=6, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
+                     chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=1, geometry="vessel",
+                     radius=6.0, depth=4, geo_seed=0, n_modes=31, mode_seed=0),
     "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
                       chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
                       n_modes=0, mode_seed=0),
