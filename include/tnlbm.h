@@ -24,8 +24,8 @@
  *     tnlbm_mps_offset(L, cap, k); inside the slot the core is packed
  *     [r_k][2][r_(k+1)] row-major with its realised bonds r.  Realised bonds
  *     are an int32 array r[0..L] with r[0] = r[L] = 1.
- *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32 and TNLBM_TF32
- *     buffers float.
+ *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32, TNLBM_TF32 and
+ *     TNLBM_MIXED buffers float.
  *   - stream arguments are cudaStream_t values passed as void* (NULL = legacy
  *     default stream).  Primitive calls are asynchronous on that stream unless
  *     stated; they allocate their own scratch with cudaMalloc and free it
@@ -52,7 +52,20 @@ enum {
   TNLBM_E_CAPACITY = -7  /* a realised bond exceeded a buffer capacity   */
 };
 
-enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2 };
+/* Precision of a simulation or primitive call:
+ *   TNLBM_FP64   cores, contractions, QR and SVD in FP64
+ *   TNLBM_FP32   FP32 cores, contractions, QR and one-sided Jacobi SVD; the
+ *                singular-value tails and the rank rule in FP64
+ *   TNLBM_TF32   as TNLBM_FP32, with the fit's core contractions on the tensor
+ *                cores (TF32 operands, FP32 sums)
+ *   TNLBM_MIXED  FP32 cores, contractions and QR sweeps; the centre SVD of every
+ *                rounding step (Eq. svd-move: the singular values whose tail is
+ *                the discarded weight, and the kept singular vectors) by an
+ *                FP64 one-sided Jacobi on the FP32 centre matrix, with the
+ *                Gram sums, norms and tails in FP64.  On one GPU the Jacobi of
+ *                a rounding is shared by a thread-block cluster of up to 16
+ *                CTAs (tnlbm_config.max_cluster). */
+enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2, TNLBM_MIXED = 3 };
 enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
 enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1, TNLBM_HADAMARD_ZIPUP = 2 };
 
@@ -79,12 +92,12 @@ typedef struct {
   int chi_max;             /* bond cap chi of every rounding (Sec. 2.1)        */
   double eps;              /* relative rounding tolerance: keep the smallest
                               rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
-  int precision;           /* TNLBM_FP64, TNLBM_FP32, or TNLBM_TF32 (FP32
-                              storage; the fit's core contractions on the
-                              tensor cores with TF32 operands, FP32 sums).
-                              Near tau = 1/2 (weakly damped flows) the FP32
-                              one-sided Jacobi of the roundings leaves errors
-                              the collision does not damp: use TNLBM_FP64  */
+  int precision;           /* TNLBM_FP64, TNLBM_FP32, TNLBM_TF32 or TNLBM_MIXED
+                              (see the enum above).  Near tau = 1/2 (weakly
+                              damped flows) the FP32 one-sided Jacobi of
+                              TNLBM_FP32 / TNLBM_TF32 leaves errors the
+                              collision does not damp: use TNLBM_MIXED or
+                              TNLBM_FP64                                       */
   int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default), _EXACT
                               (Eq. mul followed by a rounding) or _ZIPUP (the
                               zip-up pass, then a rounding; chi_max <= 512)     */
@@ -118,6 +131,27 @@ typedef struct {
   int block_sums;          /* 1: the moments as one rounding of the block sum of
                               all Q populations (Eq. add over all terms) instead
                               of the pairwise tree; needs Q chi_max <= 1024     */
+  int learned_rank;        /* learned rounding from the start (not in the paper):
+                              0 off; 1 log spectra and training rows (as
+                              tnlbm_learn_configure mode 1); 3 randomized
+                              truncation at the previous step's rank (mode 3).
+                              Mode 2 (the rank model) needs a trained model:
+                              tnlbm_learn_set_mlp, then tnlbm_learn_configure.
+                              The Gaussian test matrix is drawn from `seed`;
+                              oversampling 8, one power step, eta 0.2           */
+  uint64_t seed;           /* seed of that test matrix (SplitMix64 stream,
+                              Box-Muller normals)                               */
+  int jacobi_max_sweeps;   /* sweep limit of every one-sided Jacobi SVD (0 = 60);
+                              a rounding that reaches it makes tnlbm_step return
+                              TNLBM_E_NOCONV                                   */
+  long long wait_limit_ns; /* limit of every wait between the CTAs of a cluster
+                              (0 = 5 s); running out makes tnlbm_step return
+                              TNLBM_E_TIMEOUT (the simulation can be destroyed) */
+  int max_cluster;         /* CTAs per rounding job for the FP64 centre SVDs
+                              (TNLBM_MIXED and TNLBM_FP64): 0 = automatic (the
+                              largest of 16, 8, 4, 2 at which every job of a
+                              dependency level is resident at once), 1 = one
+                              CTA per job, else a cap (power of two <= 16)      */
 } tnlbm_config;
 
 enum { TNLBM_FACE_WALL = 0, TNLBM_FACE_VELOCITY = 1, TNLBM_FACE_PRESSURE = 2 };
@@ -173,6 +207,14 @@ int tnlbm_stats_get(tnlbm_sim *s, tnlbm_stats *out);
 /* Inlet velocity u_b of a TNLBM_FACE_VELOCITY face (0..5) from the next step
  * on (a time-dependent inflow sets it before every step); synchronous. */
 int tnlbm_set_face_velocity(tnlbm_sim *s, int face, const double *u);
+
+/* Change the Jacobi sweep limit and the cross-CTA wait limit of every rounding
+ * of the simulation's step from the next step on (meaning and defaults as the
+ * tnlbm_config members jacobi_max_sweeps and wait_limit_ns; >= 0).  A step
+ * whose Jacobi reaches the limit returns TNLBM_E_NOCONV, one whose wait runs
+ * out TNLBM_E_TIMEOUT; either way the simulation stays valid for
+ * tnlbm_destroy (its populations are then unreliable).  Synchronous. */
+int tnlbm_set_limits(tnlbm_sim *s, int jacobi_max_sweeps, long long wait_limit_ns);
 
 /* Advance k steps through the captured graph and return the device time of
  * the k launches in *ms (CUDA events on the simulation's stream). */

@@ -33,22 +33,6 @@ int cuda_fail(cudaError_t e, const char* what) {
   return TNLBM_E_CUDA;
 }
 
-static int status_to_code(const int* st8) {
-  const int st = st8[0];
-  if (st & ST_NOCONV && !(st & (ST_CAPACITY | ST_NAN | ST_TIMEOUT))) {
-    char buf[160];
-    snprintf(buf, sizeof(buf), "Jacobi SVD reached its sweep limit (job %d, site %d, %d columns of length %d)",
-             st8[2], st8[3], st8[4], st8[5]);
-    set_error(buf);
-    return TNLBM_E_NOCONV;
-  }
-  if (st & ST_CAPACITY) { set_error("a realised bond exceeded a buffer capacity"); return TNLBM_E_CAPACITY; }
-  if (st & ST_NAN) { set_error("non-finite values in a rounding"); return TNLBM_E_NAN; }
-  if (st & ST_TIMEOUT) { set_error("bounded device wait ran out"); return TNLBM_E_TIMEOUT; }
-  if (st & ST_NOCONV) { set_error("Jacobi SVD reached its sweep limit"); return TNLBM_E_NOCONV; }
-  return 0;
-}
-
 // ---------------------------------------------------------------- lattices
 struct LatticeDef {
   int Q;
@@ -144,6 +128,7 @@ struct tnlbm_sim {
     FitJob* d_fj = nullptr;
     ZipJob* d_zj = nullptr;
     bool has_rho0 = false;
+    int cluster = 1;               // CTAs per rounding job of this level
   };
   std::vector<Level> levels;
   MpsRef* d_rho_ref = nullptr;
@@ -459,6 +444,22 @@ struct Builder {
   }
 };
 
+// Options every rounding job of a simulation carries.
+static void set_round_options(const tnlbm_sim* s, RoundJob& rj) {
+  rj.svd64 = s->prec == TNLBM_MIXED ? 1 : 0;
+  rj.max_sweeps = s->cfg.jacobi_max_sweeps;
+  rj.wait_ns = s->cfg.wait_limit_ns;
+}
+
+// CTAs per rounding job for a launch of njobs jobs of a simulation: clusters
+// share the FP64 centre SVDs (TNLBM_MIXED and TNLBM_FP64); FP32 jobs run alone.
+template <typename T>
+static int sim_cluster(const tnlbm_sim* s, int njobs) {
+  if (s->prec != TNLBM_MIXED && s->prec != TNLBM_FP64) return 1;
+  const int cap = s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16;
+  return cap <= 1 ? 1 : round_cluster_size<T>(njobs, cap);
+}
+
 template <typename T>
 static int upload_levels(tnlbm_sim* s) {
   // group specs by level, materialise RoundJobs / FitJobs with scratch shared across levels
@@ -486,6 +487,7 @@ static int upload_levels(tnlbm_sim* s) {
       }
       rj.dst = s->nodes[js.out];
       rj.discard = s->d_discard;
+      set_round_options(s, rj);
       plan_round_job(rj, s->L, s->n, sizeof(T));
       lvl_round[js.level] += rj.lay.total;
       lv.rj.push_back(rj);
@@ -545,6 +547,7 @@ static int upload_levels(tnlbm_sim* s) {
       lv.d_rj = (RoundJob*)s->arena.alloc(lv.rj.size() * sizeof(RoundJob));
       if (!lv.d_rj) return TNLBM_E_OOM;
       cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice);
+      lv.cluster = sim_cluster<T>(s, (int)lv.rj.size());
     }
     if (!lv.fj.empty()) {
       lv.d_fj = (FitJob*)s->arena.alloc(lv.fj.size() * sizeof(FitJob));
@@ -580,7 +583,7 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
     }
     if (!lv.rj.empty()) {
       launch_round<T>(lv.d_rj, (int)lv.rj.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal,
-                      s->d_status, s->s0, ctr, s->learn_mode ? s->d_learn : nullptr);
+                      s->d_status, s->s0, ctr, s->learn_mode ? s->d_learn : nullptr, lv.cluster);
       if (prof) prof->mark(C_ROUND);
       ++n;
     }
@@ -695,7 +698,7 @@ template <typename T>
 static int run_round_now(tnlbm_sim* s, std::vector<RoundJob>& jobs) {
   if (jobs.empty()) return 0;
   size_t tot = 0;
-  for (auto& j : jobs) { plan_round_job(j, s->L, s->n, sizeof(T)); tot += j.lay.total; }
+  for (auto& j : jobs) { set_round_options(s, j); plan_round_job(j, s->L, s->n, sizeof(T)); tot += j.lay.total; }
   T* scr = nullptr;
   RoundJob* dj = nullptr;
   if (cudaMalloc(&scr, std::max<size_t>(tot, 1) * sizeof(T)) != cudaSuccess) return TNLBM_E_OOM;
@@ -703,7 +706,8 @@ static int run_round_now(tnlbm_sim* s, std::vector<RoundJob>& jobs) {
   for (auto& j : jobs) { j.scratch = scr + o; o += j.lay.total; }
   if (cudaMalloc(&dj, jobs.size() * sizeof(RoundJob)) != cudaSuccess) { cudaFree(scr); return TNLBM_E_OOM; }
   cudaMemcpy(dj, jobs.data(), jobs.size() * sizeof(RoundJob), cudaMemcpyHostToDevice);
-  launch_round<T>(dj, (int)jobs.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal, s->d_status, s->s0);
+  launch_round<T>(dj, (int)jobs.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal, s->d_status, s->s0,
+                  nullptr, nullptr, sim_cluster<T>(s, (int)jobs.size()));
   cudaError_t e = cudaStreamSynchronize(s->s0);
   cudaFree(scr);
   cudaFree(dj);
@@ -931,8 +935,18 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (!(C.tau > 0.5)) { set_error("tau must exceed 0.5"); return TNLBM_E_ARG; }
   if (C.chi_max < 1 || C.chi_max > 512) { set_error("chi_max must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.eps < 0.0) { set_error("eps must be >= 0"); return TNLBM_E_ARG; }
-  if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32 && C.precision != TNLBM_TF32) {
+  if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32 && C.precision != TNLBM_TF32 &&
+      C.precision != TNLBM_MIXED) {
     set_error("bad precision");
+    return TNLBM_E_ARG;
+  }
+  if (C.jacobi_max_sweeps < 0 || C.wait_limit_ns < 0 || C.max_cluster < 0 || C.max_cluster > 16 ||
+      (C.max_cluster & (C.max_cluster - 1)) != 0) {
+    set_error("jacobi_max_sweeps, wait_limit_ns >= 0; max_cluster 0 or a power of two <= 16");
+    return TNLBM_E_ARG;
+  }
+  if (C.learned_rank != 0 && C.learned_rank != 1 && C.learned_rank != 3) {
+    set_error("learned_rank must be 0, 1 or 3 (the rank model is set with tnlbm_learn_set_mlp)");
     return TNLBM_E_ARG;
   }
   if (C.hadamard != TNLBM_HADAMARD_FIT && C.hadamard != TNLBM_HADAMARD_EXACT && C.hadamard != TNLBM_HADAMARD_ZIPUP) {
@@ -972,6 +986,28 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   s->cfg.mask_cores = nullptr;
   s->cfg.mask_ranks = nullptr;
   s->cfg.modes = nullptr;
+  if (!rc && C.learned_rank > 0) {
+    // Gaussian test matrix of the randomized truncation from the seed:
+    // SplitMix64 uniforms in (0, 1], Box-Muller pairs
+    const int rows = 2 * C.chi_max, ld = C.chi_max + 8;
+    std::vector<double> om((size_t)rows * ld);
+    uint64_t x = C.seed;
+    auto next = [&x]() {
+      uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      return ((double)(z >> 11) + 1.0) * (1.0 / 9007199254740992.0);
+    };
+    for (size_t i = 0; i < om.size(); i += 2) {
+      const double u1 = next(), u2 = next();
+      const double rad = std::sqrt(-2.0 * std::log(u1)), th = 6.283185307179586 * u2;
+      om[i] = rad * std::cos(th);
+      if (i + 1 < om.size()) om[i + 1] = rad * std::sin(th);
+    }
+    rc = tnlbm_learn_configure(s, C.learned_rank, om.data(), rows, ld, 8, 1, 0.2,
+                               C.precision == TNLBM_FP64 ? 1e-12 : 1e-5, C.learned_rank == 1 ? 65536 : 0);
+  }
   if (rc) {
     std::string msg = tn::g_err;
     tnlbm_destroy(s);
@@ -1218,6 +1254,25 @@ int tnlbm_learn_counters(tnlbm_sim* s, long long* out, int reset) {
   return 0;
 }
 
+int tnlbm_set_limits(tnlbm_sim* s, int jacobi_max_sweeps, long long wait_limit_ns) {
+  if (!s || jacobi_max_sweeps < 0 || wait_limit_ns < 0) {
+    set_error("bad arguments to tnlbm_set_limits");
+    return TNLBM_E_ARG;
+  }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  s->cfg.jacobi_max_sweeps = jacobi_max_sweeps;
+  s->cfg.wait_limit_ns = wait_limit_ns;
+  for (auto& lv : s->levels) {
+    if (lv.rj.empty()) continue;
+    for (auto& rj : lv.rj) {
+      rj.max_sweeps = jacobi_max_sweeps;
+      rj.wait_ns = wait_limit_ns;
+    }
+    TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
+  }
+  return 0;
+}
+
 int tnlbm_set_face_velocity(tnlbm_sim* s, int face, const double* u) {
   if (!s || face < 0 || face > 5 || !u) { set_error("bad arguments to tnlbm_set_face_velocity"); return TNLBM_E_ARG; }
   if (s->cfg.face_kind[face] != TNLBM_FACE_VELOCITY) {
@@ -1274,13 +1329,14 @@ struct RsvdArgs {               // randomized truncation at given target ranks
 template <typename T>
 static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* terms, void* const* dst,
                         int* const* dst_ranks, int dst_cap, int chi, double eps, int materialize,
-                        cudaStream_t st, const RsvdArgs* ra = nullptr) {
+                        cudaStream_t st, const RsvdArgs* ra = nullptr, int svd64 = 0) {
   const int L = 3 * n_bits;
   std::vector<RoundJob> jobs(batch);
   std::vector<T> masks;
   for (int b = 0; b < batch; ++b) {
     RoundJob& j = jobs[b];
     j = RoundJob{};
+    j.svd64 = svd64;
     j.nterms = nterms;
     j.chi = chi;
     j.eps = eps;
@@ -1357,8 +1413,9 @@ static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* ter
   if (!masks.empty()) TN_CUDA(cudaMemcpyAsync(dm.p, masks.data(), masks.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   TN_CUDA(cudaMemsetAsync(ds.p, 0, STATUS_INTS * sizeof(int), st));
   TN_CUDA(cudaMemsetAsync(dsc.p, 0, SC_COUNT * sizeof(double), st));
+  const int cl = (!materialize && (svd64 || sizeof(T) == 8)) ? round_cluster_size<T>(batch, 16) : 1;
   launch_round<T>((const RoundJob*)dj.p, batch, L, n_bits, (const T*)dm.p, (const double*)dsc.p, (int*)ds.p, st,
-                  nullptr, ra ? (const LearnCtx*)dlc.p : nullptr);
+                  nullptr, ra ? (const LearnCtx*)dlc.p : nullptr, cl);
   TN_CUDA(cudaGetLastError());
   int rc = check_status((int*)ds.p, st);
   if (ra && ra->counters) {
@@ -1473,7 +1530,8 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const 
                         void* const* dst, int* const* dst_ranks, int dst_cap, int chi_max, double eps,
                         void* stream) {
   if (n_bits < 1 || n_bits > 10 || batch < 0 || nterms < 1 || nterms > TN_MAXT || !terms || !dst ||
-      !dst_ranks || chi_max < 1 || chi_max > dst_cap || chi_max > 512 || eps < 0) {
+      !dst_ranks || chi_max < 1 || chi_max > dst_cap || chi_max > 512 || eps < 0 || precision < TNLBM_FP64 ||
+      precision > TNLBM_MIXED) {
     set_error("bad arguments to tnlbm_lincomb_round");
     return TNLBM_E_ARG;
   }
@@ -1481,7 +1539,8 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const 
   cudaStream_t st = (cudaStream_t)stream;
   return precision == TNLBM_FP64
              ? tn::lincomb_impl<double>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st)
-             : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st);
+             : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st,
+                                       nullptr, precision == TNLBM_MIXED ? 1 : 0);
 }
 
 int tnlbm_lincomb_round_rsvd(int precision, int n_bits, int batch, int nterms, const tnlbm_term* terms,
@@ -1699,6 +1758,7 @@ struct tnlbm_batch {
     std::vector<FitGroup> fg;      // indexed like lens
     RoundJob* d_rj = nullptr;
     std::vector<int> rho0;         // simulations with a rho_0 node at this level
+    int cluster = 1;               // CTAs per rounding job of this level
   };
   std::vector<Level> levels;
   int* d_status = nullptr;
@@ -1740,7 +1800,8 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
       }
     }
     if (!lv.rj.empty()) {
-      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->lens.back(), 0, nullptr, nullptr, b->d_status, b->s0);
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->lens.back(), 0, nullptr, nullptr, b->d_status, b->s0,
+                      nullptr, nullptr, lv.cluster);
       ++nl;
     }
     if (any_fit)
@@ -1814,6 +1875,10 @@ static int batch_build(tnlbm_batch* b) {
       lv.d_rj = (RoundJob*)b->arena.alloc(lv.rj.size() * sizeof(RoundJob));
       if (!lv.d_rj) return TNLBM_E_OOM;
       TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
+      int cap = 16;
+      for (tnlbm_sim* s : b->sims) cap = std::min(cap, s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16);
+      lv.cluster = (b->prec == TNLBM_MIXED || b->prec == TNLBM_FP64) && cap > 1
+                       ? round_cluster_size<T>((int)lv.rj.size(), cap) : 1;
     }
     for (auto& g : lv.fg) {
       if (g.fj.empty()) continue;

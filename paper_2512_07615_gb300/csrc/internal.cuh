@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdio.h>
 
 #include <string>
 #include <vector>
@@ -87,6 +88,7 @@ struct Term {
 struct RoundLayout {
   size_t q_off[TN_MAXL + 1];  // left-orthogonal cores of the QR sweep
   size_t w_off, m_off, r_off, c_off, jw_off, jv_off, us_off, rz_off, qw_off, total;
+  size_t jw64_off, jv64_off;  // FP64 Jacobi matrices (in elements of T; = jw/jv for T = double)
 };
 
 // Learned-rank rounding state shared by all jobs of a launch (nullable parts).
@@ -134,6 +136,9 @@ struct RoundJob {
   const double* scal;         // scalars of this job's simulation, or null = launch's
   int L, n_bits;              // chain length and bits per axis of this job, or 0 = launch's
   double* discard;            // accumulator of squared discarded tails (device), or null
+  int svd64;                  // 1: centre SVDs in FP64 on FP32 data (precision TNLBM_MIXED)
+  int max_sweeps;             // Jacobi sweep limit (0 = 60)
+  long long wait_ns;          // limit of every cross-CTA wait in ns (0 = 5 s)
 };
 
 // bound of one term's bond k from the capacities of its operands
@@ -152,7 +157,8 @@ __host__ __device__ inline int term_bond_bound(const Term& t, int L, int n_bits,
   return 0;
 }
 
-// Fill rw/qb bounds and the scratch layout of a job (host side).
+// Fill rw/qb bounds and the scratch layout of a job (host side); j.svd64 must
+// be set before (it adds the FP64 Jacobi matrices for FP32 data).
 void plan_round_job(RoundJob& j, int L, int n_bits, size_t elem_bytes);
 
 // ------------------------------------------------------------ error helpers
@@ -165,13 +171,41 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::tn::cuda_fail(_e, #call); \
   } while (0)
 
+// Error code and message of a device status block (STATUS_INTS ints).  A
+// timed-out wait comes first: whatever follows it in the launch is unreliable
+// (a CTA that gave up skips its work), so NaN or capacity flags raised after it
+// are consequences.  A sweep limit alone is reported with where it happened.
+inline int status_to_code(const int* st8) {
+  const int st = st8[0];
+  if (st & ST_TIMEOUT) { set_error("a bounded wait between the CTAs of a cluster ran out"); return TNLBM_E_TIMEOUT; }
+  if (st & ST_NOCONV && !(st & (ST_CAPACITY | ST_NAN))) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "Jacobi SVD reached its sweep limit (job %d, site %d, %d columns of length %d)",
+             st8[2], st8[3], st8[4], st8[5]);
+    set_error(buf);
+    return TNLBM_E_NOCONV;
+  }
+  if (st & ST_CAPACITY) { set_error("a realised bond exceeded a buffer capacity"); return TNLBM_E_CAPACITY; }
+  if (st & ST_NAN) { set_error("non-finite values in a rounding"); return TNLBM_E_NAN; }
+  if (st & ST_NOCONV) { set_error("Jacobi SVD reached its sweep limit"); return TNLBM_E_NOCONV; }
+  return 0;
+}
+
 // ------------------------------------------------------------ launchers
 // Rounding / materialisation of `njobs` jobs already resident on the device.
+// cluster: CTAs per job (1 = one CTA; > 1 = a thread-block cluster whose CTAs
+// share the FP64 Jacobi of the job; see round_cluster_size).
 template <typename T>
 void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits,
                   const T* d_masks, const double* d_scal, int* d_status,
-                  cudaStream_t st, double* d_ctr = nullptr, const LearnCtx* d_learn = nullptr);
+                  cudaStream_t st, double* d_ctr = nullptr, const LearnCtx* d_learn = nullptr,
+                  int cluster = 1);
 size_t round_smem_bytes();
+// CTAs per job for a launch of njobs rounding jobs whose centre SVDs run in
+// FP64: the largest cluster size (<= cap, power of two, <= 16) at which all
+// njobs clusters are resident at once on the current device; 1 if none.
+template <typename T>
+int round_cluster_size(int njobs, int cap);
 // increments the device step counter read by the rank model
 void launch_learn_tick(int* d_step, cudaStream_t st);
 

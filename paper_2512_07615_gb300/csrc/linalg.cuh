@@ -735,45 +735,72 @@ __device__ T qr_noise_floor2(const T* A, int m, int n, int lda, T* red) {
   return (T)m * f * f;
 }
 
+// Squared-norm floor of the Householder columns below which a column counts
+// as zero.  FP64 data: m (4 eps max|A|)^2, its rounding noise.  FP32 data: the
+// column norms, beta and tau are formed in FP64 (no squares underflow), so
+// only columns below 2^-60 of the largest entry, or with norm under 1e-36
+// (the edge of the FP32 range), are zero: small columns of a matrix with a
+// wide spread of column scales (a mixed-canonical centre carries its singular
+// values in its columns) are kept.
+template <typename T>
+__device__ double qr_zero_floor2(const T* A, int m, int n, int lda, T* red) {
+  if constexpr (sizeof(T) == 8) {
+    return (double)qr_noise_floor2<T>(A, m, n, lda, red);
+  } else {
+    T amax = (T)0;
+    for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x)
+      amax = fmax(amax, fabs(A[(size_t)(idx / n) * lda + idx % n]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    T mx = (T)0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) mx = fmax(mx, red[w]);
+    __syncthreads();
+    const double f = 8.673617379884035e-19 * (double)mx;     // 2^-60 max|A|
+    return fmax((double)m * f * f, 1e-72);
+  }
+}
+
 template <typename T>
 __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
                                    double* tau, T* wv, double* red, T* vb, T* wb) {
   const int kk = imin(m, n);
   const int G = 8;                                 // threads per column in the panel dots
-  __shared__ T s_scale, s_norm2;
+  __shared__ T s_scale;
+  __shared__ double s_norm2;
   __shared__ T sT[QB][QB + 1], sG[QB][QB + 1];
   __shared__ signed char s_dneg[1024];
   T* redT = (T*)red;
   T* wpart = wb;
   T* W = wb + (size_t)QNG * QB * n;
-  // columns below the rounding floor of the matrix are zero: a reflector built
-  // from them (with squares near the underflow range) is not orthogonal and
-  // would spoil the larger columns it is applied to
-  const T floor2 = qr_noise_floor2<T>(A, m, n, lda, redT);
+  // columns below the zero floor: a reflector built from them would not be
+  // orthogonal and would spoil the larger columns it is applied to
+  const double floor2 = qr_zero_floor2<T>(A, m, n, lda, redT);
   for (int p0 = 0; p0 < kk; p0 += QB) {
     const int pe = imin(p0 + QB, kk), pb = pe - p0;
-    {                                              // norm of column p0 below its diagonal
-      T part = (T)0;
+    {                                              // norm of column p0 below its diagonal (FP64 sum)
+      double part = 0.0;
       for (int i = p0 + 1 + threadIdx.x; i < m; i += blockDim.x) {
-        const T v = A[(size_t)i * lda + p0];
+        const double v = (double)A[(size_t)i * lda + p0];
         part += v * v;
       }
-      const T t = block_sum_t<T>(part, redT);
+      const double t = block_sum(part, red);
       if (threadIdx.x == 0) s_norm2 = t;
     }
     // ---- panel: column by column, updates restricted to the panel
     for (int j = p0; j < pe; ++j) {
       if (threadIdx.x == 0) {
-        const T sig2 = s_norm2;
-        const T alpha = A[(size_t)j * lda + j];
+        const double sig2 = s_norm2;
+        const double alpha = (double)A[(size_t)j * lda + j];
         if (sig2 <= floor2) {
           tau[j] = 0.0;
-          s_scale = sig2 == (T)0 ? (T)0 : (T)-1;    // -1: zero the column below the diagonal
+          s_scale = sig2 == 0.0 ? (T)0 : (T)-1;    // -1: zero the column below the diagonal
         } else {
-          const T beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
-          tau[j] = (double)((beta - alpha) / beta);
-          s_scale = (T)1 / (alpha - beta);
-          A[(size_t)j * lda + j] = beta;
+          const double beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
+          tau[j] = (beta - alpha) / beta;
+          s_scale = (T)(1.0 / (alpha - beta));
+          A[(size_t)j * lda + j] = (T)beta;
         }
       }
       __syncthreads();
@@ -796,7 +823,7 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
         }
         __syncthreads();
       }
-      T part = (T)0;
+      double part = 0.0;
       if (tj != (T)0) {
         const int rows = m - j;
         if (nc > 0) {
@@ -805,19 +832,19 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
             const T vi = (ii == j) ? (T)1 : sc * A[(size_t)ii * lda + j];
             const T nv = A[(size_t)ii * lda + c] - wv[c] * vi;
             A[(size_t)ii * lda + c] = nv;
-            if (c == j + 1 && ii > j + 1) part += nv * nv;
+            if (c == j + 1 && ii > j + 1) part += (double)nv * (double)nv;
           }
         }
         __syncthreads();
         for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
       } else if (nc > 0) {
         for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) {
-          const T v = A[(size_t)i * lda + j + 1];
+          const double v = (double)A[(size_t)i * lda + j + 1];
           part += v * v;
         }
       }
       if (j + 1 < pe) {
-        const T t = block_sum_t<T>(part, redT);
+        const double t = block_sum(part, red);
         if (threadIdx.x == 0) s_norm2 = t;
       } else {
         __syncthreads();

@@ -430,7 +430,9 @@ __global__ void __launch_bounds__(1024) gram_eig_kernel(double* G, int m, double
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     double a = 0.0;
     for (int i = 0; i < m; ++i) a += Wm[(size_t)j * m + i] * Wm[(size_t)j * m + i];
-    lam[j] = sqrt(a);                         // eigenvalue of G = sigma^2 of M
+    const double lj = sqrt(a);                // eigenvalue of G = sigma^2 of M
+    if (!(lj >= 0.0) || isinf(lj)) { lam[j] = -1.0; atomicOr(status, ST_NAN); }   // orders last
+    else lam[j] = lj;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < m; j += blockDim.x) {

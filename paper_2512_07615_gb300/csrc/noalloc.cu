@@ -22,6 +22,7 @@
 // capture that includes this entry point.
 #include <cstring>
 
+#include "fit.cuh"
 #include "internal.cuh"
 
 #define TN_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -34,7 +35,7 @@ namespace tn {
 static __device__ __align__(256) unsigned char g_na_scratch[TN_NOALLOC_SCRATCH_BYTES];
 static __device__ __align__(256) RoundJob g_na_jobs[TN_NOALLOC_MAX_JOBS];
 static __device__ __align__(256) double g_na_masks[TN_NOALLOC_MAX_MASKS * TN_MAXL * 2];
-static __device__ __align__(256) double g_na_scal[8];
+static __device__ __align__(256) double g_na_scal[SC_COUNT];   // the full scalar table a rounding reads
 static __device__ __align__(256) int g_na_status[STATUS_INTS];
 
 struct NoallocPtrs {
@@ -157,17 +158,15 @@ static int noalloc_impl(int n_bits, int batch, int nterms, const tnlbm_term* ter
   if (nmask > 0)
     TN_CUDA(cudaMemcpyAsync(P->masks, masks, (size_t)nmask * TN_MAXL * 2 * sizeof(T),
                             cudaMemcpyHostToDevice, st));
-  TN_CUDA(cudaMemsetAsync(P->scal, 0, 8 * sizeof(double), st));
+  TN_CUDA(cudaMemsetAsync(P->scal, 0, SC_COUNT * sizeof(double), st));
   TN_CUDA(cudaMemsetAsync(P->status, 0, STATUS_INTS * sizeof(int), st));
   launch_round<T>(P->jobs, batch, L, n_bits, (const T*)P->masks, P->scal, P->status, st);
   TN_CUDA(cudaGetLastError());
-  TN_CUDA(cudaStreamSynchronize(st));
+  // the status word is read on the caller's stream, which alone is waited for
   int h[STATUS_INTS] = {0};
-  TN_CUDA(cudaMemcpy(h, P->status, sizeof(h), cudaMemcpyDeviceToHost));
-  if (h[0] & ST_CAPACITY) { set_error("a realised bond exceeded a buffer capacity"); return TNLBM_E_CAPACITY; }
-  if (h[0] & ST_NAN) { set_error("non-finite values in a rounding"); return TNLBM_E_NAN; }
-  if (h[0] & ST_NOCONV) { set_error("Jacobi SVD reached its sweep limit"); return TNLBM_E_NOCONV; }
-  return 0;
+  TN_CUDA(cudaMemcpyAsync(h, P->status, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TN_CUDA(cudaStreamSynchronize(st));
+  return status_to_code(h);
 }
 
 }  // namespace tn

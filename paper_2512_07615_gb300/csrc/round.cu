@@ -8,6 +8,9 @@
 // (left-orthogonalising sweep, Eq. lorg).  The right-to-left sweep then moves the
 // canonical centre back to site 0 with SVDs (Eq. svd-move) and truncates at the
 // centre to chi / eps.
+#include <algorithm>
+
+#include "cluster.cuh"
 #include "linalg.cuh"
 
 namespace tn {
@@ -73,6 +76,22 @@ void plan_round_job(RoundJob& j, int L, int n_bits, size_t eb) {
   j.lay.us_off = al(us);
   j.lay.rz_off = al(rz);
   j.lay.qw_off = al(qw);
+  if (eb == 8) {
+    j.lay.jw64_off = j.lay.jw_off;                 // the FP64 Jacobi matrices are the Jacobi matrices
+    j.lay.jv64_off = j.lay.jv_off;
+  } else if (j.svd64) {
+    size_t w64 = 0, v64 = 0;                       // doubles, in units of T (two floats each)
+    for (int k = 0; k < L; ++k) {
+      const int rn = imin(j.chi, j.qb[k + 1]);
+      const int ncol = imin(j.qb[k], 2 * rn), len = imax(j.qb[k], 2 * rn);
+      w64 = std::max(w64, (size_t)ncol * jacobi_ld<double>(len));
+      v64 = std::max(v64, (size_t)ncol * jacobi_ld<double>(ncol));
+    }
+    j.lay.jw64_off = al(2 * w64);
+    j.lay.jv64_off = al(2 * v64);
+  } else {
+    j.lay.jw64_off = j.lay.jv64_off = 0;
+  }
   j.lay.total = off;
 }
 
@@ -197,14 +216,494 @@ struct PhaseClock {
   }
 };
 
+// ---------------------------------------------------------------- row-partitioned FP64 SVD
+// Work-area layout (bytes, same in every CTA of the cluster) of svd64_rows:
+// the CTA's rows of W and V, the column norms, per-pair rotations, the
+// exchange buffers of the pair inner products and of the column norms, and
+// the singular values / order / tails the rank rule reads.
+struct RowsLayout {
+  int lw, lv, npairs;
+  size_t wl, vl, nrm, pc, ps, pf, xb, nbuf, sig, perm, tail, total;
+};
+__host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
+  RowsLayout R;
+  R.lw = (len + P - 1) / P;
+  R.lv = (ncol + P - 1) / P;
+  R.npairs = (ncol + 1) / 2;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~(size_t)15; return r; };
+  R.wl = take((size_t)ncol * R.lw * 8);
+  R.vl = take((size_t)ncol * R.lv * 8);
+  R.nrm = take((size_t)ncol * 8);
+  R.pc = take((size_t)R.npairs * 8);
+  R.ps = take((size_t)R.npairs * 8);
+  R.pf = take((size_t)R.npairs * 4);
+  R.xb = take((size_t)2 * R.npairs * P * 8);
+  R.nbuf = take((size_t)ncol * P * 8);
+  R.sig = take((size_t)ncol * 8);
+  R.perm = take((size_t)ncol * 4);
+  R.tail = take((size_t)(ncol + 2) * 8);
+  R.total = o;
+  return R;
+}
+
+// round-robin pair p of round rnd over np (even) indices, a < b
+__device__ __forceinline__ void rr_pair(int rnd, int p, int np, int& a, int& b) {
+  if (p == 0) { a = rnd; b = np - 1; }
+  else { a = (rnd + p) % (np - 1); b = (rnd - p + (np - 1)) % (np - 1); }
+  if (a > b) { const int t = a; a = b; b = t; }
+}
+
+// Column norms of W over the cluster: every CTA adds its rows, sends the
+// partial sums to every CTA, and sums them in rank order (the same order, so
+// the same doubles, in every CTA).  Ends with nrm[] valid everywhere.
+__device__ inline void rows_norms(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, int ncol, int li) {
+  const double* Wl = (const double*)(wa + R.wl);
+  double* nb = (double*)(wa + R.nbuf);
+  double* nrm = (double*)(wa + R.nrm);
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
+  const unsigned mask8 = 0xffu << (threadIdx.x & 24);
+  // stores into the other CTAs follow the last cluster barrier by at most a
+  // round, far less than a CTA that gave up waits at the exit barrier
+  const bool alive = !cc.dead;
+  for (int j0 = 0; j0 < ncol; j0 += ngrp) {
+    const int j = j0 + grp;
+    double v = 0.0;
+    if (j < ncol)
+      for (int ii = gl; ii < li; ii += 8) { const double x = Wl[(size_t)j * R.lw + ii]; v += x * x; }
+    v += __shfl_xor_sync(mask8, v, 4, 8);
+    v += __shfl_xor_sync(mask8, v, 2, 8);
+    v += __shfl_xor_sync(mask8, v, 1, 8);
+    if (j < ncol) {
+      if (cc.P == 1) { if (gl == 0) nb[j] = v; }
+      else if (alive)
+        for (int d = gl; d < cc.P; d += 8) cl_store_remote(nb + (size_t)j * cc.P + cc.rank, d, v);
+    }
+  }
+  cl_sync(cc);
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+    double a = 0.0;
+    for (int c = 0; c < cc.P; ++c) a += nb[(size_t)j * cc.P + c];
+    nrm[j] = a;
+  }
+  __syncthreads();
+}
+
+// This CTA's parts of the inner products of every pair of round rnd, sent to
+// every CTA's exchange slots xq[p][rank]; then the cluster barrier.
+__device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, const double* Wl, double* xq, int rnd,
+                                      int np, int ncol, int li) {
+  const int npairs = np / 2;
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
+  const unsigned mask8 = 0xffu << (threadIdx.x & 24);
+  const bool alive = !cc.dead;
+  for (int p0 = 0; p0 < npairs; p0 += ngrp) {
+    const int p = p0 + grp;
+    double g = 0.0;
+    if (p < npairs) {
+      int a, b;
+      rr_pair(rnd, p, np, a, b);
+      if (b < ncol)
+        for (int ii = gl; ii < li; ii += 8) g += Wl[(size_t)a * R.lw + ii] * Wl[(size_t)b * R.lw + ii];
+    }
+    g += __shfl_xor_sync(mask8, g, 4, 8);
+    g += __shfl_xor_sync(mask8, g, 2, 8);
+    g += __shfl_xor_sync(mask8, g, 1, 8);
+    if (p < npairs) {
+      if (cc.P == 1) { if (gl == 0) xq[p] = g; }
+      else if (alive)
+        for (int d = gl; d < cc.P; d += 8) cl_store_remote(xq + (size_t)p * cc.P + cc.rank, d, g);
+    }
+  }
+  return cl_sync(cc);
+}
+
+// FP64 one-sided Jacobi SVD of the centre matrix C (m x n, T, global) with the
+// rows of the Jacobi matrices split over the CTAs of the cluster and held in
+// shared memory.  W = the columns of C (n <= m) or of C^T, scaled by scl; V
+// accumulates the rotations.  CTA c owns entries [c len / P, (c+1) len / P)
+// of every column of W and [c ncol / P, (c+1) ncol / P) of every column of V.
+// Per round of the round-robin tournament each CTA forms its parts of the
+// pair inner products gamma, all CTAs exchange them (shared::cluster stores,
+// one cluster barrier) and sum them in rank order, so every CTA takes the same
+// rotations and applies them to its rows.  A pair rotates unless gamma^2 <=
+// tol^2 alpha beta (tol = 16 eps sqrt(len), as the single-CTA Jacobi); its
+// angle t = tan(theta) is Rutishauser's, evaluated in FP32 (in FP64 where
+// |zeta| > 1e18), and the rotation
+// itself is orthogonal to FP64 accuracy (c = (1 + t^2)^(-1/2) by two FP64
+// Newton steps from the FP32 value, s = c t), so W and V stay exactly
+// rotated while an angle that is off by FP32 round-off only leaves a residual
+// the next sweeps remove.  Column norms follow the rotations exactly
+// (c^2 alpha - 2cs gamma + s^2 beta) and are recomputed at the start of every
+// sweep and at the end.  Every CTA then finds the same singular values, order
+// and kept rank (the rank rule of Eq. svd-move with delta) and writes its rows
+// of core k (V^T[:r], r x n) and of U S (m x r).  Called by all threads of
+// every CTA with equal arguments; returns the kept rank (0 if it exceeds the
+// bond capacity) and the sweeps.
 template <typename T>
-__global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L_arg,
-                                                   int n_bits_arg, const T* __restrict__ masks_arg,
-                                                   const double* __restrict__ scal_arg,
-                                                   int* __restrict__ status,
-                                                   double* __restrict__ ctr,
-                                                   const LearnCtx* __restrict__ lc) {
-  const RoundJob& J = jobs[blockIdx.x];
+__device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m, int n, double scl, double delta,
+                          int maxsw, int* sweeps_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* wa = smem + SM_SMALL;
+  T* scr = (T*)J.scratch;
+  const T* C = scr + J.lay.c_off;
+  T* US = scr + J.lay.us_off;
+  T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
+  const int ncol = imin(m, n), len = imax(m, n);
+  const bool trans = (n <= m);
+  const RowsLayout R = rows_layout(ncol, len, cc.P);
+  double* Wl = (double*)(wa + R.wl);
+  double* Vl = (double*)(wa + R.vl);
+  double* nrm = (double*)(wa + R.nrm);
+  double* xb = (double*)(wa + R.xb);
+  double* sig = (double*)(wa + R.sig);
+  int* perm = (int*)(wa + R.perm);
+  double* tail = (double*)(wa + R.tail);
+  const int i0 = cc.rank * len / cc.P, li = (cc.rank + 1) * len / cc.P - i0;
+  const int v0 = cc.rank * ncol / cc.P, vi = (cc.rank + 1) * ncol / cc.P - v0;
+  // own rows of W (promoted, scaled) and of V = I
+  for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
+    const int j = idx / li, ii = idx % li, i = i0 + ii;
+    const T v = trans ? __ldcg(C + (size_t)i * n + j) : __ldcg(C + (size_t)j * n + i);
+    Wl[(size_t)j * R.lw + ii] = scl * (double)v;
+  }
+  for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
+    const int j = idx / vi, ii = idx % vi;
+    Vl[(size_t)j * R.lv + ii] = (j == v0 + ii) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = (ncol + 1) & ~1, npairs = np / 2;
+  const double tol = 16.0 * 2.220446049250313e-16 * sqrt((double)len);
+  const double tol2 = tol * tol;
+  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
+  int sweep = 0;
+  unsigned q = 0;                                  // rounds so far (exchange buffer parity)
+  if (ncol >= 2) {
+    for (; sweep < maxsw; ++sweep) {
+      rows_norms(cc, R, wa, ncol, li);
+      int rot = 0;
+      bool ok = rows_pair_dots(cc, R, Wl, xb + (size_t)(q & 1) * npairs * cc.P, 0, np, ncol, li);
+      for (int rnd = 0; rnd < np - 1 && ok; ++rnd, ++q) {
+        const double* xq = xb + (size_t)(q & 1) * npairs * cc.P;
+        // a group of 8 lanes per pair: the same sum, angle and rotation in
+        // every CTA.  Lane l adds the partials of CTAs l, l + 8 (in that order)
+        // and the lanes' sums are combined by a fixed xor tree, so every CTA
+        // forms gamma identically; lane 0 takes the angle and the new norms,
+        // the group rotates.
+        for (int p0 = 0; p0 < npairs; p0 += ngrp) {
+          const int p = p0 + grp;
+          const unsigned mask8 = 0xffu << (threadIdx.x & 24);
+          int a = 0, b = ncol;
+          double g = 0.0;
+          if (p < npairs) {
+            rr_pair(rnd, p, np, a, b);
+            for (int c = gl; c < cc.P; c += 8) g += xq[(size_t)p * cc.P + c];
+          }
+          g += __shfl_xor_sync(mask8, g, 4, 8);
+          g += __shfl_xor_sync(mask8, g, 2, 8);
+          g += __shfl_xor_sync(mask8, g, 1, 8);
+          if (p >= npairs || b >= ncol) continue;
+          double cs = 1.0, sn = 0.0;
+          int go = 0;
+          if (gl == 0) {
+            const double al = nrm[a], be = nrm[b];
+            if (g != 0.0 && al > 1e-250 && be > 1e-250 && g * g > tol2 * al * be) {
+              // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); for |zeta| > 1e18 (a
+              // column near zero against a large one) t = 1 / (2 zeta) in FP64,
+              // where the FP32 quotient would overflow and stall the rotation at 0
+              const double zd = (be - al) / (2.0 * g);
+              double t;
+              if (fabs(zd) > 1e18) {
+                t = 0.5 / zd;
+              } else {
+                const float zeta = (float)zd;
+                const float az = fabsf(zeta);
+                t = (double)copysignf(1.f / (az + sqrtf(1.f + zeta * zeta)), zeta);
+              }
+              const double x = 1.0 + t * t;
+              cs = (double)rsqrtf((float)x);
+              cs = cs * (1.5 - 0.5 * x * cs * cs);
+              cs = cs * (1.5 - 0.5 * x * cs * cs);
+              sn = cs * t;
+              const double c2 = cs * cs, s2 = sn * sn, csg = 2.0 * cs * sn * g;
+              nrm[a] = c2 * al - csg + s2 * be;
+              nrm[b] = s2 * al + csg + c2 * be;
+              go = 1;
+            }
+          }
+          go = __shfl_sync(mask8, go, 0, 8);
+          if (!go) continue;
+          cs = __shfl_sync(mask8, cs, 0, 8);
+          sn = __shfl_sync(mask8, sn, 0, 8);
+          for (int ii = gl; ii < li; ii += 8) {
+            double* pa = Wl + (size_t)a * R.lw + ii;
+            double* pb = Wl + (size_t)b * R.lw + ii;
+            const double u = *pa, w = *pb;
+            *pa = cs * u - sn * w;
+            *pb = sn * u + cs * w;
+          }
+          for (int ii = gl; ii < vi; ii += 8) {
+            double* pa = Vl + (size_t)a * R.lv + ii;
+            double* pb = Vl + (size_t)b * R.lv + ii;
+            const double u = *pa, w = *pb;
+            *pa = cs * u - sn * w;
+            *pb = sn * u + cs * w;
+          }
+          rot = 1;
+        }
+        __syncthreads();
+        if (rnd + 1 < np - 1)
+          ok = rows_pair_dots(cc, R, Wl, xb + (size_t)((q + 1) & 1) * npairs * cc.P, rnd + 1, np, ncol, li);
+      }
+      const int any = __syncthreads_or(rot);
+      if (!any || cc.dead) break;
+    }
+  }
+  *sweeps_out = cc.dead ? maxsw : sweep;
+  // exact norms -> singular values, order and rank (identical in every CTA);
+  // non-finite values order last and are reported
+  rows_norms(cc, R, wa, ncol, li);
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+    const double sv = sqrt(nrm[j]) / scl;
+    if (!(sv >= 0.0) || isinf(sv)) { sig[j] = -1.0; atomicOr(cc.status, ST_NAN); }
+    else sig[j] = sv;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+    int rank = 0;
+    const double sj = sig[j];
+    for (int o = 0; o < ncol; ++o) rank += (sig[o] > sj) || (sig[o] == sj && o < j);
+    perm[rank] = j;
+  }
+  __syncthreads();
+  __shared__ int s_r;
+  if (threadIdx.x == 0) {
+    const int rmax = imin(J.chi, ncol);
+    double tail2 = 0.0;
+    for (int p = ncol - 1; p >= 1; --p) {
+      const double sv = sig[perm[p]];
+      tail2 += sv * sv;
+      tail[2 + p] = tail2;
+    }
+    int rr = rmax;
+    for (int qq = 1; qq <= rmax; ++qq) {
+      const double t2 = (qq < ncol) ? tail[2 + qq] : 0.0;
+      if (sqrt(t2) <= delta) { rr = qq; break; }
+    }
+    s_r = rr > bond_cap(L, J.dst.cap, k) ? 0 : rr;
+  }
+  __syncthreads();
+  const int r = s_r;
+  if (r > 0 && !cc.dead) {
+    if (trans) {
+      // core: rows of V^T (entries c in this CTA's V rows); U S: this CTA's rows of W
+      for (int idx = threadIdx.x; idx < r * vi; idx += blockDim.x) {
+        const int jr = idx / vi, ii = idx % vi;
+        __stcg(out + (size_t)jr * n + v0 + ii, (T)Vl[(size_t)perm[jr] * R.lv + ii]);
+      }
+      for (int idx = threadIdx.x; idx < li * r; idx += blockDim.x) {
+        const int ii = idx / r, jr = idx % r;
+        __stcg(US + (size_t)(i0 + ii) * r + jr, (T)(Wl[(size_t)perm[jr] * R.lw + ii] * (1.0 / scl)));
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < r * li; idx += blockDim.x) {
+        const int jr = idx / li, ii = idx % li;
+        const int pj = perm[jr];
+        const double sg = sig[pj] * scl;
+        const double v = sg > 0.0 ? Wl[(size_t)pj * R.lw + ii] / sg : (i0 + ii == jr ? 1.0 : 0.0);
+        __stcg(out + (size_t)jr * n + i0 + ii, (T)v);
+      }
+      for (int idx = threadIdx.x; idx < vi * r; idx += blockDim.x) {
+        const int ii = idx / r, jr = idx % r;
+        const int pj = perm[jr];
+        __stcg(US + (size_t)(v0 + ii) * r + jr, (T)(Vl[(size_t)pj * R.lv + ii] * sig[pj]));
+      }
+    }
+  }
+  cl_sync(cc);
+  return r;
+}
+
+// Shared-memory pointers of the leader CTA that the FP64 centre SVD uses.
+struct SiteShared {
+  double* red;
+  double* tau;     // [1] scale, [2..] tails
+  double* sig;
+  int* perm;
+  int* bad;
+  int* rank;
+  double* flops;
+};
+
+// Centre SVD of one right-to-left step in FP64 (FP32 data promoted, or FP64
+// data on a cluster): C (m x n, T, global) = U S V^T by one-sided Jacobi in
+// FP64 on the columns of C (n <= m) or of C^T; the rank rule and the
+// discarded tail in FP64; writes core k = V^T[:r] (r x n) to out and U S
+// (m x r) to US, both in T.  The Jacobi matrices sit in the leader's shared
+// memory when the job has one CTA and they fit, else in the job's global
+// scratch, where every CTA of the cluster works on them.  Returns the kept
+// rank, or 0 after flagging an error.
+template <typename T>
+__device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T* C, int m, int n, T* out, T* US,
+                                       T* scr, T* work, const SiteShared& sh, ClusterCtx& cc, int* status,
+                                       const LearnCtx* lc, PhaseClock& pc, double delta) {
+  const int ncol = imin(m, n), len = imax(m, n);
+  const bool trans = (n <= m);
+  const int ldw = jacobi_ld<double>(len), ldv = jacobi_ld<double>(ncol);
+  const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(double);
+  const bool in_smem = cc.P == 1 && need <= (size_t)SM_WORK;
+  double* Wm = in_smem ? (double*)work : (double*)(scr + J.lay.jw64_off);
+  double* Vm = in_smem ? (double*)work + (size_t)ncol * ldw : (double*)(scr + J.lay.jv64_off);
+  // exact power-of-two scale so that max |C| is in [1, 2) (as the T path)
+  T amax = (T)0;
+  for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) amax = fmax(amax, fabs(C[idx]));
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5] = (double)amax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a = fmax(a, sh.red[w]);
+    int e = 0;
+    if (a > 0.0 && isfinite(a)) frexp(a, &e);
+    sh.tau[1] = ldexp(1.0, 1 - e);
+  }
+  __syncthreads();
+  const double scl = sh.tau[1];
+  const int maxsw = J.max_sweeps > 0 ? J.max_sweeps : 60;
+  if (!in_smem && cc.P > 1 && rows_layout(ncol, len, cc.P).total <= (size_t)SM_WORK) {
+    // rows of the Jacobi matrices spread over the cluster, in shared memory
+    pc.lap(PH_SVD_OUT);
+    cl_command(cc, 2, ncol, len, maxsw, m, n, k, delta, scl);
+    int sw = 0;
+    const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw);
+    pc.lap(PH_JACOBI);
+    const RowsLayout R = rows_layout(ncol, len, cc.P);
+    const unsigned char* wa = (const unsigned char*)work;
+    const double* sig = (const double*)(wa + R.sig);
+    const int* perm = (const int*)(wa + R.perm);
+    const double* tail = (const double*)(wa + R.tail);
+    if (threadIdx.x == 0) {
+      pc.acc[6] += sw; pc.acc[7] += 1.0;
+      if (sw >= maxsw) {
+        flag(status, ST_NOCONV);
+        if (atomicCAS(&status[1], 0, 1) == 0) {
+          status[2] = blockIdx.x / cc.P; status[3] = k; status[4] = ncol; status[5] = len;
+        }
+      }
+      if (r == 0) flag(status, ST_CAPACITY);
+      else {
+        if (J.discard && r < ncol) atomicAdd(J.discard, tail[2 + r]);
+        J.dst.ranks[k] = r;
+      }
+      *sh.flops += svd_flops(m, n);
+      if (lc && lc->counters) atomicAdd(&lc->counters[2], 1);
+    }
+    // singular values and order where the spectrum log reads them
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) { sh.sig[j] = sig[j]; sh.perm[j] = perm[j]; }
+    // the other CTAs wrote rows of the core and of U S at L2: read them back
+    // past this SM's L1 before the leader's own loads use them
+    if (r > 0) {
+      for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) out[idx] = __ldcg(out + idx);
+      for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) US[idx] = __ldcg(US + idx);
+    }
+    __syncthreads();
+    return r;
+  }
+  for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
+    const int jj = idx / len, i = idx % len;
+    const double v = scl * (double)(trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]);
+    if (in_smem) Wm[(size_t)jj * ldw + i] = v;
+    else __stcg(Wm + (size_t)jj * ldw + i, v);
+  }
+  __syncthreads();
+  pc.lap(PH_SVD_OUT);
+  const double jac0 = pc.acc[PH_JACOBI];
+  int sw;
+  if (in_smem) {
+    sw = jacobi_cols_fast<double>(Wm, ldw, Vm, ldv, ncol, len, maxsw);
+  } else {
+    cl_command(cc, 1, ncol, len, maxsw);
+    sw = jacobi64_cluster(cc, Wm, ldw, Vm, ldv, ncol, len, maxsw);
+  }
+  pc.lap(PH_JACOBI);
+  if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }
+  if (threadIdx.x == 0 && !in_smem) { pc.acc[8] += pc.acc[PH_JACOBI] - jac0; pc.acc[9] += 1.0; }
+  if (sw >= maxsw && threadIdx.x == 0) {
+    flag(status, ST_NOCONV);
+    if (atomicCAS(&status[1], 0, 1) == 0) {
+      status[2] = blockIdx.x / cc.P; status[3] = k; status[4] = ncol; status[5] = len;
+    }
+  }
+  auto ldW = [&](size_t i) -> double { return in_smem ? Wm[i] : __ldcg(Wm + i); };
+  auto ldV = [&](size_t i) -> double { return in_smem ? Vm[i] : __ldcg(Vm + i); };
+  for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+    double a = 0.0;
+    for (int i = 0; i < len; ++i) { const double w = ldW((size_t)jj * ldw + i); a += w * w; }
+    const double sv = sqrt(a) / scl;
+    if (!(sv >= 0.0) || isinf(sv)) { sh.sig[jj] = -1.0; flag(status, ST_NAN); }   // orders last
+    else sh.sig[jj] = sv;
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
+    int rank = 0;
+    const double sj = sh.sig[jj];
+    for (int o = 0; o < ncol; ++o) {
+      const double so = sh.sig[o];
+      rank += (so > sj) || (so == sj && o < jj);
+    }
+    sh.perm[rank] = jj;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int rmax = imin(J.chi, ncol);
+    double tail2 = 0.0;
+    int rr = rmax;
+    for (int p = ncol - 1; p >= 1; --p) {
+      const double sv = sh.sig[sh.perm[p]];
+      tail2 += sv * sv;
+      sh.tau[2 + p] = tail2;
+    }
+    for (int q = 1; q <= rmax; ++q) {
+      const double t2 = (q < ncol) ? sh.tau[2 + q] : 0.0;
+      if (sqrt(t2) <= delta) { rr = q; break; }
+    }
+    if (rr > bond_cap(L, J.dst.cap, k)) { *sh.bad = 1; rr = bond_cap(L, J.dst.cap, k); }
+    *sh.rank = rr;
+    if (J.discard && rr < ncol) atomicAdd(J.discard, sh.tau[2 + rr]);
+    *sh.flops += svd_flops(m, n);
+    if (lc && lc->counters) atomicAdd(&lc->counters[2], 1);
+  }
+  __syncthreads();
+  if (*sh.bad) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return 0; }
+  const int r = *sh.rank;
+  for (int idx = threadIdx.x; idx < r * n; idx += blockDim.x) {
+    const int jr = idx / n, c = idx % n;
+    const int pj = sh.perm[jr];
+    double v;
+    if (trans) {
+      v = ldV((size_t)pj * ldv + c);
+    } else {
+      const double sg = sh.sig[pj] * scl;
+      v = sg > 0.0 ? ldW((size_t)pj * ldw + c) / sg : (c == jr ? 1.0 : 0.0);
+    }
+    out[idx] = (T)v;
+  }
+  for (int idx = threadIdx.x; idx < m * r; idx += blockDim.x) {
+    const int i = idx / r, jr = idx % r;
+    const int pj = sh.perm[jr];
+    US[idx] = (T)(trans ? ldW((size_t)pj * ldw + i) * (1.0 / scl) : ldV((size_t)pj * ldv + i) * sh.sig[pj]);
+  }
+  if (threadIdx.x == 0) J.dst.ranks[k] = r;
+  __syncthreads();
+  return r;
+}
+
+// The rounding job as run by the leader CTA of its cluster (the whole job
+// when the cluster has one CTA).
+template <typename T>
+__device__ void round_job_body(const RoundJob& J, int L_arg, int n_bits_arg, const T* __restrict__ masks_arg,
+                               const double* __restrict__ scal_arg, int* __restrict__ status,
+                               double* __restrict__ ctr, const LearnCtx* __restrict__ lc, ClusterCtx& cc) {
   // per-job chain length, mask table and scalars (jobs of several simulations,
   // possibly of different lattice sizes, in one launch)
   const int L = J.L > 0 ? J.L : L_arg;
@@ -380,7 +879,8 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
     T* US = scr + J.lay.us_off;
     int r = 0;
-    bool done = false;
+    bool done = false;             // randomized truncation accepted
+    bool full64 = false;           // full SVD taken in FP64 (svd64_site)
     // ---- randomized truncation at a target rank, certified (learned-rank path)
     int tgt = 0;
     if (J.rsvd_mode && lc != nullptr && lc->omega != nullptr) {
@@ -463,7 +963,9 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
         T a = (T)0;
         const T* w = Wm + (size_t)jj * ldw;
         for (int i = 0; i < n; ++i) a += w[i] * w[i];
-        s_sig[jj] = (double)sqrt(a) / scl;
+        const double sv = (double)sqrt(a) / scl;
+        if (!(sv >= 0.0) || isinf(sv)) { s_sig[jj] = -1.0; flag(status, ST_NAN); }   // orders last
+        else s_sig[jj] = sv;
       }
       __syncthreads();
       for (int jj = threadIdx.x; jj < l; jj += blockDim.x) {
@@ -524,7 +1026,14 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
     }
     // ---- full SVD (reference path, and fallback of the randomized one)
     const int ncol = imin(m, n), len = imax(m, n);
-    if (!done) {
+    if (!done && (J.svd64 || (sizeof(T) == 8 && cc.P > 1))) {
+      if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
+      const SiteShared sh{s_red, s_tau, s_sig, s_perm, &s_bad, &s_rank, &s_flops};
+      r = svd64_site<T>(J, L, k, C, m, n, out, US, scr, work, sh, cc, status, lc, pc, delta);
+      if (r == 0) return;
+      full64 = true;
+    }
+    if (!done && !full64) {
       if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
       const bool trans = (n <= m);             // Jacobi on the columns of C
       // 16-byte row strides (vector loads in the Jacobi); shared memory if it fits
@@ -556,7 +1065,7 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
         Wm[(size_t)jj * ldw_e + i] = tscl * (trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]);
       }
       __syncthreads();
-      const int maxsw = 60;
+      const int maxsw = J.max_sweeps > 0 ? J.max_sweeps : 60;
       pc.lap(PH_SVD_OUT);
       const double jac0 = pc.acc[PH_JACOBI];
       int sw = jacobi_cols_fast<T>(Wm, ldw_e, Vm, ldv_e, ncol, len, maxsw);
@@ -569,14 +1078,16 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
       if (sw >= maxsw && threadIdx.x == 0) {
         flag(status, ST_NOCONV);
         if (atomicCAS(&status[1], 0, 1) == 0) {     // first failure: where and how big
-          status[2] = blockIdx.x; status[3] = k; status[4] = ncol; status[5] = len;
+          status[2] = blockIdx.x / cc.P; status[3] = k; status[4] = ncol; status[5] = len;
         }
       }
       for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
         T a = (T)0;
         const T* w = Wm + (size_t)jj * ldw_e;
         for (int i = 0; i < len; ++i) a += w[i] * w[i];
-        s_sig[jj] = (double)sqrt(a) / scl;         // singular value of the unscaled C
+        const double sv = (double)sqrt(a) / scl;   // singular value of the unscaled C
+        if (!(sv >= 0.0) || isinf(sv)) { s_sig[jj] = -1.0; flag(status, ST_NAN); }   // orders last
+        else s_sig[jj] = sv;
       }
       __syncthreads();
       for (int jj = threadIdx.x; jj < ncol; jj += blockDim.x) {
@@ -704,24 +1215,126 @@ __global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ 
   }
 }
 
+// Worker CTA (rank > 0 of a cluster): joins the leader's FP64 Jacobi runs
+// until the leader sends the exit command or a wait runs out.
+template <typename T>
+__device__ void round_worker(const RoundJob& J, int L_arg, ClusterCtx& cc) {
+  T* scr = (T*)J.scratch;
+  double* Wm = (double*)(scr + J.lay.jw64_off);
+  double* Vm = (double*)(scr + J.lay.jv64_off);
+  const int L = J.L > 0 ? J.L : L_arg;
+  for (;;) {
+    if (!cl_sync(cc)) break;
+    const volatile ClusterCmd* cmd = (const volatile ClusterCmd*)&cc.sh->cmd;
+    const int op = cmd->op, ncol = cmd->ncol, len = cmd->len, maxsw = cmd->maxsw;
+    const int m = cmd->m, n = cmd->n, k = cmd->k;
+    const double delta = cmd->delta, scl = cmd->scl;
+    __syncthreads();
+    if (op == 1) {
+      jacobi64_cluster(cc, Wm, jacobi_ld<double>(len), Vm, jacobi_ld<double>(ncol), ncol, len, maxsw);
+    } else if (op == 2) {
+      int sw = 0;
+      svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw);
+    } else {
+      break;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RT) round_kernel(const RoundJob* __restrict__ jobs, int L_arg,
+                                                   int n_bits_arg, const T* __restrict__ masks_arg,
+                                                   const double* __restrict__ scal_arg,
+                                                   int* __restrict__ status,
+                                                   double* __restrict__ ctr,
+                                                   const LearnCtx* __restrict__ lc) {
+  __shared__ ClusterShared s_cl;
+  ClusterCtx cc;
+  const RoundJob& J = jobs[blockIdx.x / cl_size()];
+  cl_init(cc, &s_cl, status, J.wait_ns > 0 ? J.wait_ns : 5000000000LL);
+  if (cc.rank == 0) {
+    round_job_body<T>(J, L_arg, n_bits_arg, masks_arg, scal_arg, status, ctr, lc, cc);
+    cl_command(cc, 0, 0, 0, 0);
+  } else {
+    round_worker<T>(J, L_arg, cc);
+  }
+  cl_exit(cc);
+}
+
 template <typename T>
 void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T* d_masks,
                   const double* d_scal, int* d_status, cudaStream_t st, double* d_ctr,
-                  const LearnCtx* d_learn) {
+                  const LearnCtx* d_learn, int cluster) {
   if (njobs <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)round_smem_bytes());
+    cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     attr_set = true;
   }
-  round_kernel<T><<<njobs, RT, round_smem_bytes(), st>>>(d_jobs, L, n_bits, d_masks, d_scal,
-                                                         d_status, d_ctr, d_learn);
+  if (cluster <= 1) {
+    round_kernel<T><<<njobs, RT, round_smem_bytes(), st>>>(d_jobs, L, n_bits, d_masks, d_scal,
+                                                           d_status, d_ctr, d_learn);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * cluster, 1, 1);
+  cfg.blockDim = dim3(RT, 1, 1);
+  cfg.dynamicSmemBytes = round_smem_bytes();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, round_kernel<T>, d_jobs, L, n_bits, d_masks, d_scal, d_status, d_ctr, d_learn);
+}
+
+template <typename T>
+int round_cluster_size(int njobs, int cap) {
+  // resident clusters of each size on this device (queried once per device)
+  static int cached_dev = -1;
+  static int max_active[5] = {0, 0, 0, 0, 0};      // sizes 1, 2, 4, 8, 16
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev != cached_dev) {
+    cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)round_smem_bytes());
+    cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int e = 0; e < 5; ++e) {
+      const int P = 1 << e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(P, 1, 1);
+      cfg.blockDim = dim3(RT, 1, 1);
+      cfg.dynamicSmemBytes = round_smem_bytes();
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = P;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, round_kernel<T>, &cfg) != cudaSuccess) n = 0;
+      max_active[e] = n;
+    }
+    cudaGetLastError();
+    cached_dev = dev;
+  }
+  for (int e = 4; e >= 1; --e) {
+    const int P = 1 << e;
+    if (P <= cap && max_active[e] >= njobs) return P;
+  }
+  return 1;
 }
 
 template void launch_round<float>(const RoundJob*, int, int, int, const float*, const double*,
-                                  int*, cudaStream_t, double*, const LearnCtx*);
+                                  int*, cudaStream_t, double*, const LearnCtx*, int);
 template void launch_round<double>(const RoundJob*, int, int, int, const double*,
-                                   const double*, int*, cudaStream_t, double*, const LearnCtx*);
+                                   const double*, int*, cudaStream_t, double*, const LearnCtx*, int);
+template int round_cluster_size<float>(int, int);
+template int round_cluster_size<double>(int, int);
 
 }  // namespace tn

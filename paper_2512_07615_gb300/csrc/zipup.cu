@@ -246,7 +246,9 @@ __global__ void __launch_bounds__(ZT) zipup_kernel(const ZipJob* __restrict__ jo
       T acc = (T)0;
       const T* w = Wm + (size_t)j * ldw;
       for (int i = 0; i < kk; ++i) acc += w[i] * w[i];
-      s_sig[j] = (double)sqrt(acc) / scl;
+      const double sv = (double)sqrt(acc) / scl;
+      if (!(sv >= 0.0) || isinf(sv)) { s_sig[j] = -1.0; zflag(status, ST_NAN); }   // orders last
+      else s_sig[j] = sv;
     }
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {

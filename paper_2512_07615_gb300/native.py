@@ -8,7 +8,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtnlbm.so")
 
-FP64, FP32, TF32 = 0, 1, 2
+FP64, FP32, TF32, MIXED = 0, 1, 2, 3
 D3Q19, D3Q15 = 19, 15
 FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
 HADAMARD_FIT, HADAMARD_EXACT, HADAMARD_ZIPUP = 0, 1, 2
@@ -47,6 +47,11 @@ class Config(ctypes.Structure):
         ("face_u", (ctypes.c_double * 3) * 6),
         ("face_rho", ctypes.c_double * 6),
         ("block_sums", ctypes.c_int),
+        ("learned_rank", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("jacobi_max_sweeps", ctypes.c_int),
+        ("wait_limit_ns", ctypes.c_longlong),
+        ("max_cluster", ctypes.c_int),
     ]
 
 
@@ -98,6 +103,7 @@ SIGNATURES = {
     "tnlbm_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
     "tnlbm_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tnlbm_step_timed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p]),
+    "tnlbm_set_limits": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong]),
     "tnlbm_profile_step": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p, c_int_p, c_double_p]),
     "tnlbm_last_error": (ctypes.c_char_p, []),
     "tnlbm_mps_size": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),

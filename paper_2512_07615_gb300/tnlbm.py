@@ -8,7 +8,7 @@ import torch
 
 from . import native as nat
 
-_DT = {nat.FP64: torch.float64, nat.FP32: torch.float32, nat.TF32: torch.float32}
+_DT = {nat.FP64: torch.float64, nat.FP32: torch.float32, nat.TF32: torch.float32, nat.MIXED: torch.float32}
 
 
 def mps_size(L, cap):
@@ -314,7 +314,8 @@ def mask_product(outer, inner, cap, chi_max, eps, stream=None):
 def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), solid=None,
                 chi_mask=16, eps_mask=1e-12, mask_cores=None, force=(0.0, 0.0, 0.0), chi_max=16,
                 eps=1e-10, precision=nat.FP64, hadamard=nat.HADAMARD_FIT, sweeps=2, modes=None,
-                conserve_mass=False, faces=None, block_sums=False):
+                conserve_mass=False, faces=None, block_sums=False, learned_rank=0, seed=0,
+                jacobi_max_sweeps=0, wait_limit_ns=0, max_cluster=0):
     """tnlbm_config for the arguments; returns (config, arrays the config
     points to, which must stay alive until the simulation is created).
     faces: None (bounce-back on every wall face) or a dict face -> (kind, u_b,
@@ -353,6 +354,11 @@ def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), soli
     c.sweeps = sweeps
     c.conserve_mass = int(bool(conserve_mass))
     c.block_sums = int(bool(block_sums))
+    c.learned_rank = int(learned_rank)
+    c.seed = int(seed)
+    c.jacobi_max_sweeps = int(jacobi_max_sweeps)
+    c.wait_limit_ns = int(wait_limit_ns)
+    c.max_cluster = int(max_cluster)
     for f6, (kind, u_b, rho_b) in (faces or {}).items():
         c.face_kind[f6] = int(kind)
         for d in range(3):
@@ -494,6 +500,12 @@ class Sim:
         out = (ctypes.c_longlong * 3)()
         nat.check(nat.lib().tnlbm_learn_counters(self.h, out, int(reset)), "tnlbm_learn_counters")
         return tuple(out)
+
+    def set_limits(self, jacobi_max_sweeps=0, wait_limit_ns=0):
+        """Jacobi sweep limit and cross-CTA wait limit (ns) of the step's
+        roundings from the next step on (0 = defaults 60 and 5 s)."""
+        nat.check(nat.lib().tnlbm_set_limits(self.h, int(jacobi_max_sweeps), int(wait_limit_ns)),
+                  "tnlbm_set_limits")
 
     def set_face_velocity(self, face, u):
         """Inlet velocity of a velocity face from the next step on."""

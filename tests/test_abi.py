@@ -99,7 +99,7 @@ def test_argument_errors_of_the_newer_entry_points(lib):
     c.tau = 0.8
     c.chi_max = 8
     c.eps = 1e-8
-    c.precision = 3                     # no such precision
+    c.precision = 7                     # no such precision
     assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
     assert b"precision" in lib.tnlbm_last_error()
     c.precision = nat.TF32
@@ -114,3 +114,29 @@ def test_argument_errors_of_the_newer_entry_points(lib):
     c.block_sums = 1                    # 19 x 64 > 1024: the summed bond of one rounding
     assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
     assert b"block_sums" in lib.tnlbm_last_error()
+
+
+def test_argument_errors_of_the_precision_and_failure_options(lib):
+    """Mixed precision, the learned-rank and seed members, the Jacobi sweep
+    cap, the wait limit and the cluster cap reject bad values before any
+    device call."""
+    import paper_2512_07615_gb300.native as nat
+    h = ctypes.c_void_p()
+    c = nat.Config()
+    c.n_per_axis = 3
+    c.lattice = 19
+    c.tau = 0.8
+    c.chi_max = 8
+    c.eps = 1e-8
+    c.precision = nat.MIXED
+    for field, bad in (("max_cluster", 3), ("max_cluster", 32), ("max_cluster", -1),
+                       ("jacobi_max_sweeps", -1), ("wait_limit_ns", -5)):
+        setattr(c, field, bad)
+        assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1, field
+        assert b"max_cluster" in lib.tnlbm_last_error()
+        setattr(c, field, 0)
+    c.learned_rank = 2                  # the rank model needs a trained network first
+    assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
+    assert b"learned_rank" in lib.tnlbm_last_error()
+    # primitives: precision beyond the enum
+    assert lib.tnlbm_lincomb_round(9, 3, 1, 1, None, None, None, 8, 8, 0.0, None) == -1
