@@ -3,26 +3,36 @@
 Default workload (the configuration the metric is quoted on): porous medium,
 128^3 D3Q19 BGK, tau = 0.7, seeded sphere pack (radius 10 cells, 35 % solid,
 periodic), mask compressed as an MPS (chi_mask = 64), body force 1e-5 along x
-standing in for the pressure drive, chi_max = 64, FP32 storage and contractions
-with FP64 singular-value tails, variational products (2 sweeps), and a smooth
-rank-saturating start (31 seeded Fourier modes of density and velocity, so
-bonds sit at chi from the first step).
+standing in for the pressure drive, chi_max = 64, precision TNLBM_MIXED (FP32
+cores, contractions and QR sweeps; every centre SVD an FP64 one-sided Jacobi
+shared by a thread-block cluster), variational products (2 sweeps), and a
+smooth rank-saturating start (31 seeded Fourier modes of density and
+velocity, so bonds sit at chi from the first step).
 
 Prints one JSON line (rank 0):
-  value      represented MLUPS = N^3 * steps / device seconds, all ranks
-  e2e        the same through the C ABI with the populations copied host ->
-             device before and device -> host after every step
-  roofline   dominant kernel class of one profiled step against its peak
-  cpu_baseline  the CPU oracle on a bounded sample of the same step
-  clocks     nvidia-smi samples taken during the timed region
-  batched    eight 64^3 simulations stepped in one graph, against the same
-             eight one after another and one plain FP64 full-SVD simulation
+  value        represented MLUPS = N^3 * steps / device seconds, all ranks
+  vs_baseline  value / that of the plain FP64 unbatched full-SVD GPU path on the
+               same workload (the baseline the metric names)
+  rel_l2_u     ||u - u_64|| / ||u_64|| against that FP64 path after the same
+               steps from the same start
+  e2e          the same metric through the C ABI with the populations copied
+               host -> device before and device -> host after every step
+  roofline     the rounding kernel (the dominant one) against its peak
+  cpu_baseline the CPU oracle timed on one whole step of the timed state
+  clocks       nvidia-smi samples taken during the timed region
+  batched      eight 64^3 simulations stepped in one graph (FP32)
 
---impl reference times the CPU oracle instead (the reference arm).
+--impl reference times the CPU oracle instead (the reference arm): one oracle
+step of the workload's start is recorded call by call (roundings and products
+with their inputs), and every bench step replays a fifth of those calls, so
+that 5 bench steps re-run one whole oracle step.
+--probe-peaks measures the FP32 (no TF32), TF32 and FP64 GEMM peaks with
+torch.matmul (the record the roofline reads is profiles/peaks_gb300.md).
 Multi-GPU: independent replicas, one per rank (nothing is exchanged).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -35,28 +45,30 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "mixed": 3}
+PREC_NAME = {v: k for k, v in PREC.items()}
+
 WORKLOADS = {
     "porous128": dict(n=7, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
-                      chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
+                      chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=3, geometry="spheres",
                       radius=10.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
     # same chi and per-job matrix shapes as porous128 on 64^3 (for kernel captures)
     "porous64": dict(n=6, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
-                     chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=1, geometry="spheres",
+                     chi=64, eps=1e-7, chi_mask=64, eps_mask=1e-8, precision=3, geometry="spheres",
                      radius=5.0, solid_fraction=0.35, geo_seed=0, n_modes=31, mode_seed=0),
     # Taylor-Green vortex, 256^3, Re = 800 at u0 = 0.05 (nu = u0 (N / 2 pi) / Re)
     "tgv256": dict(n=8, lattice=19, tau=0.5 + 3.0 * 0.05 * (256 / (2 * 3.141592653589793)) / 800.0,
                    periodic=(1, 1, 1), force=(0.0, 0.0, 0.0), chi=64, eps=1e-7, chi_mask=1, eps_mask=1e-12,
-                   precision=1, geometry=None, n_modes=0, mode_seed=0, tgv_u0=0.05),
+                   precision=3, geometry=None, n_modes=0, mode_seed=0, tgv_u0=0.05),
     # branching vessel, 256^3: binary tree of cylinders (depth 4, Murray radii
     # from 24 cells, bifurcation half-angles 25-45 deg), body force along the
-    # root axis in the fluid; FP32 storage and contractions (no BF16 path)
+    # root axis in the fluid
     "vessel256": dict(n=8, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
-                      chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=1, geometry="vessel",
+                      chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=3, geometry="vessel",
                       radius=24.0, depth=4, geo_seed=0, n_modes=31, mode_seed=0),
-    # the vessel's per-job shapes (chi 128: 256-wide centre matrices, Jacobi in
-    # global memory) on 64^3, for kernel captures
+    # the vessel's per-job shapes (chi 128: 256-wide centre matrices) on 64^3, for kernel captures
     "vessel64": dict(n=6, lattice=19, tau=0.7, periodic=(1, 1, 1), force=(1e-5, 0.0, 0.0),
-                     chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=1, geometry="vessel",
+                     chi=128, eps=1e-7, chi_mask=128, eps_mask=1e-8, precision=3, geometry="vessel",
                      radius=6.0, depth=4, geo_seed=0, n_modes=31, mode_seed=0),
     "channel32": dict(n=5, lattice=19, tau=0.8, periodic=(1, 1, 0), force=(1e-6, 0.0, 0.0),
                       chi=16, eps=1e-10, chi_mask=1, eps_mask=1e-12, precision=0, geometry=None,
@@ -64,9 +76,54 @@ WORKLOADS = {
 }
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP32 SIMT throughput of cuBLAS SGEMM (no TF32) measured on this machine's GB300
-# (8192^3, CUDA events): the peak used for the FP32 SIMT contraction kernels.
-FP32_SIMT_MEASURED_TFLOPS = 69.8
+PEAKS_RECORD = os.path.join(ROOT, "profiles", "peaks_gb300.md")
+
+
+def load_peaks():
+    """HBM and BF16 peaks from the driver's record; FP32 (no TF32), TF32 and
+    FP64 GEMM peaks from the committed probe record (key = value lines)."""
+    peaks = {}
+    if os.path.exists(MEASURED_PEAKS):
+        peaks.update(json.load(open(MEASURED_PEAKS)))
+    if os.path.exists(PEAKS_RECORD):
+        for line in open(PEAKS_RECORD):
+            line = line.strip().strip("`")
+            if "=" in line and not line.startswith("#"):
+                k, v = [t.strip() for t in line.split("=", 1)]
+                try:
+                    peaks[k] = float(v.split()[0])
+                except ValueError:
+                    pass
+    return peaks
+
+
+def probe_peaks():
+    """FP32 (TF32 off), TF32 and FP64 dense GEMM throughput with torch.matmul,
+    CUDA events, best of 5 after 2 warm-up products."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {}
+    for name, dt, n, tf32 in (("fp32_simt_tflops", torch.float32, 8192, False),
+                              ("tf32_tflops", torch.float32, 8192, True),
+                              ("fp64_tflops", torch.float64, 4096, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        print("%s = %.1f   (torch.matmul %s %d^3, TF32 %s, best of 5: %.3f ms)"
+              % (name, out[name], str(dt).replace("torch.", ""), n, "on" if tf32 else "off", best))
+    torch.backends.cuda.matmul.allow_tf32 = False
+    return out
 
 
 def geometry(w):
@@ -83,7 +140,7 @@ def make_sim(w, solid, modes):
     return tl.Sim(w["n"], lattice=w["lattice"], tau=w["tau"], periodic=w["periodic"], solid=solid,
                   chi_mask=w["chi_mask"], eps_mask=w["eps_mask"], force=w["force"], chi_max=w["chi"],
                   eps=w["eps"], precision=w["precision"], hadamard=0, sweeps=2, modes=modes,
-                  conserve_mass=w["precision"] != 0)
+                  conserve_mass=w["precision"] != 0, max_cluster=w.get("max_cluster", 0))
 
 
 class Clocks:
@@ -135,79 +192,86 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-# ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(w, solid, modes, budget_s=25.0, pops=None):
-    """Time the oracle on the first phases of the same step (moments, rho_0,
-    Taylor 1/rho, velocity and second-order products: roundings and fits of
-    the real populations) and extrapolate to one whole step by the step's
-    counts of roundings and fits.  pops: the populations (lists of cores) of
-    the state the GPU timed, else the workload's initial state.  Returns
-    (seconds per step, description, seconds spent)."""
+# ------------------------------------------------------------------ CPU oracle
+def oracle_config(w, solid):
+    """The oracle's configuration of the workload (products by the fit; the
+    mask MPS by the oracle's own TT-SVD of the voxels at chi_mask / eps_mask)."""
     import oracle.mps as M
     import oracle.mps_lbm as ml
-    from oracle import lattice as olat
+    from oracle import lattice as olat, quantics as q
     lat = olat.get("D3Q19" if w["lattice"] == 19 else "D3Q15")
-    # job counts of one step, from a dry run of the step's structure on 2^3 cells
-    cnt = {"round": 0, "fit": 0}
-    r0, f0 = M.lincomb_round, M.hadamard_fit
+    mask = M.tt_svd(q.encode(solid.astype(np.float64)), w["chi_mask"], w["eps_mask"]) if solid is not None else None
+    return ml.Config(w["n"], lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=w["chi"],
+                     eps=w["eps"], hadamard="fit", mask=mask)
 
-    def c_round(*a, **k):
-        cnt["round"] += 1
-        return r0(*a, **k)
 
-    def c_fit(*a, **k):
-        cnt["fit"] += 1
-        return f0(*a, **k)
+def oracle_start(cfg, modes):
+    import oracle.mps_lbm as ml
+    return ml.initial_perturbed(cfg, modes) if modes is not None else ml.initial_rest(cfg)
 
-    M.lincomb_round, M.hadamard_fit = c_round, c_fit
-    try:
-        tiny_mask = M.scale(M.ones(3), 0.1) if solid is not None else None
-        tcfg = ml.Config(1, lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=4,
-                         eps=w["eps"], hadamard="fit", mask=tiny_mask)
-        ml.step(tcfg, ml.initial_rest(tcfg))
-    finally:
-        M.lincomb_round, M.hadamard_fit = r0, f0
-    n_round, n_fit = cnt["round"], cnt["fit"]
-    # the real populations of the workload (setup, not timed)
-    cfg = ml.Config(w["n"], lat, w["tau"], force=w["force"], periodic=w["periodic"], chi_max=w["chi"],
-                    eps=w["eps"], hadamard="fit", mask=None)
-    if pops is not None:
-        f = [[np.asarray(c, dtype=np.float64) for c in x] for x in pops]
-    else:
-        f = ml.initial_perturbed(cfg, modes) if modes is not None else ml.initial_rest(cfg)
-    t_round, t_fit = [], []
-    t_start = time.perf_counter()
-    # a1: moments
-    items = [(1.0, f[i]) for i in range(lat.Q)]
-    rho = None
-    while len(items) > 1 and time.perf_counter() - t_start < budget_s:
-        nxt = []
-        for p in range(0, len(items) - 1, 2):
-            t = time.perf_counter()
-            nxt.append((1.0, M.lincomb_round([items[p], items[p + 1]], cfg.chi, cfg.eps)))
-            t_round.append(time.perf_counter() - t)
-        if len(items) % 2:
-            nxt.append(items[-1])
-        items = nxt
-    rho = items[0][1]
-    # a3-a5 style products on the same fields
-    one = M.ones(cfg.L)
-    rho0 = M.inner_ones(rho) / float(cfg.N ** 3)
+
+def oracle_whole_step(w, solid, pops):
+    """Seconds of one whole oracle step (oracle.mps_lbm.step: moments, Taylor
+    1/rho, products, collision, streaming, walls and object bounce-back with
+    the mask products) on the given populations (lists of cores)."""
+    import oracle.mps_lbm as ml
+    cfg = oracle_config(w, solid)
+    f = [[np.asarray(c, dtype=np.float64) for c in x] for x in pops]
     t = time.perf_counter()
-    drho = M.lincomb_round([(1.0, rho), (-rho0, one)], cfg.chi, cfg.eps)
-    t_round.append(time.perf_counter() - t)
-    fac = [drho] + [f[i] for i in range(1, 4)]
-    for k in range(len(fac)):
-        if time.perf_counter() - t_start > budget_s and t_fit:
-            break
+    ml.step(cfg, f)
+    return time.perf_counter() - t
+
+
+class OracleReplay:
+    """One oracle step recorded call by call: every rounding (lincomb_round)
+    and product (hadamard_fit) with its inputs and its duration; replay(c)
+    re-runs the calls of chunk c of `parts` contiguous chunks of about equal
+    recorded time and returns (seconds, fraction of the step's recorded time)."""
+
+    def __init__(self, w, solid, modes, parts=5):
+        import oracle.mps as M
+        import oracle.mps_lbm as ml
+        cfg = oracle_config(w, solid)
+        f = oracle_start(cfg, modes)
+        calls = []
+        r0, f0 = M.lincomb_round, M.hadamard_fit
+
+        def rec(fn):
+            def wrapped(*a, **k):
+                t = time.perf_counter()
+                out = fn(*a, **k)
+                calls.append((fn, a, k, time.perf_counter() - t))
+                return out
+            return wrapped
+
+        M.lincomb_round, M.hadamard_fit = rec(r0), rec(f0)
+        try:
+            t = time.perf_counter()
+            ml.step(cfg, f)
+            self.record_s = time.perf_counter() - t
+        finally:
+            M.lincomb_round, M.hadamard_fit = r0, f0
+        total = sum(c[3] for c in calls)
+        self.chunks, self.frac = [], []
+        acc, cur, cur_t = 0.0, [], 0.0
+        for c in calls:
+            cur.append(c)
+            cur_t += c[3]
+            acc += c[3]
+            if acc >= total * (len(self.chunks) + 1) / parts and len(self.chunks) < parts - 1:
+                self.chunks.append(cur)
+                self.frac.append(cur_t / total)
+                cur, cur_t = [], 0.0
+        self.chunks.append(cur)
+        self.frac.append(cur_t / total)
+        self.ncalls = len(calls)
+
+    def replay(self, c):
+        c %= len(self.chunks)
         t = time.perf_counter()
-        M.hadamard_fit(fac[k], drho, 2)
-        t_fit.append(time.perf_counter() - t)
-    per_step = n_round * float(np.mean(t_round)) + n_fit * float(np.mean(t_fit))
-    desc = ("oracle (numpy FP64) on %d roundings and %d fits of the same step (moments tree and "
-            "products of the %s populations), extrapolated to the step's %d roundings and %d fits"
-            % (len(t_round), len(t_fit), "timed" if pops is not None else "initial", n_round, n_fit))
-    return per_step, desc, time.perf_counter() - t_start
+        for fn, a, k, _ in self.chunks[c]:
+            fn(*a, **k)
+        return time.perf_counter() - t, self.frac[c]
 
 
 BATCH_CHIS = (32, 48, 64, 40, 56, 32, 64, 48)
@@ -339,6 +403,43 @@ def cpu_threads():
 
 
 # ------------------------------------------------------------------ main
+def precision_desc(p):
+    return {0: dict(storage="fp64", contractions="fp64 SIMT", qr="fp64", svd="fp64 one-sided Jacobi"),
+            1: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (fp64 column norms)",
+                    svd="fp32 one-sided Jacobi, fp64 tails"),
+            2: dict(storage="fp32", contractions="tf32 tensor cores (fit), fp32 SIMT (rounding)",
+                    qr="fp32 (fp64 column norms)", svd="fp32 one-sided Jacobi, fp64 tails"),
+            3: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (fp64 column norms)",
+                    svd="fp64 one-sided Jacobi (cluster of CTAs), fp64 norms and tails")}[p]
+
+
+def reference_arm(args, w, solid, modes, config, N3, rank):
+    """The CPU oracle as the reference arm: W + K bench steps, each replaying a
+    fifth of one recorded oracle step (see OracleReplay)."""
+    if rank != 0:
+        return
+    rep = OracleReplay(w, solid, modes)
+    t_tot, cells = 0.0, 0.0
+    for i in range(args.warmup + args.steps):
+        sec, frac = rep.replay(i)
+        if i >= args.warmup:
+            t_tot += sec
+            cells += frac * N3
+    val = cells / t_tot / 1e6
+    desc = ("oracle (numpy FP64) step of the workload's start recorded call by call (%d roundings and fits, "
+            "%.1f s including its unrecorded glue); each bench step replays one fifth of those calls by "
+            "recorded time, so %d bench steps re-ran %.2f whole oracle steps"
+            % (rep.ncalls, rep.record_s, args.steps, cells / N3))
+    out = {"impl": "reference", "metric": "represented MLUPS at fixed chi", "value": val, "unit": "MLUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+           "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
+                            "sample": desc},
+           "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,17 +450,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "fp32", "tf32"], default=None,
-                    help="override the workload's precision (tf32: FP32 storage, fit contractions on the "
-                         "tensor cores with TF32 operands)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison (vs_baseline, rel_l2_u)")
+    ap.add_argument("--precision", choices=sorted(PREC), default=None,
+                    help="override the workload's precision (mixed: FP32 storage and contractions, FP64 SVD)")
+    ap.add_argument("--max-cluster", type=int, default=0, help="CTAs per rounding job cap (0 = automatic)")
     ap.add_argument("--batched-mixed", action="store_true",
                     help="also time the eight uneven simulations (64^3-256^3, chi 32-128) in one graph")
+    ap.add_argument("--probe-peaks", action="store_true", help="measure the FP32 / TF32 / FP64 GEMM peaks")
     args = ap.parse_args()
+    if args.probe_peaks:
+        probe_peaks()
+        return
     w = dict(WORKLOADS[args.workload])
     if args.precision:
-        w["precision"] = {"fp64": 0, "fp32": 1, "tf32": 2}[args.precision]
+        w["precision"] = PREC[args.precision]
+    w["max_cluster"] = args.max_cluster
     N3 = float((1 << w["n"]) ** 3)
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -371,36 +477,18 @@ def main():
         modes = synth.fourier_modes(w["n_modes"], w["mode_seed"], kmax=4, amp_rho=1e-3, amp_u=1e-3) \
             if w["n_modes"] > 0 else None
     solid = geometry(w)
-    config = {"workload": args.workload, "lattice": "D3Q%d" % w["lattice"], "cells": "%d^3" % (1 << w["n"]),
-              "chi_max": w["chi"], "chi_mask": w["chi_mask"] if solid is not None else None,
-              "eps": w["eps"], "tau": w["tau"], "products": "variational fit, 2 sweeps",
-              "storage": "fp64" if w["precision"] == 0 else "fp32",
-              "contractions": {0: "fp64 SIMT", 1: "fp32 SIMT", 2: "tf32 tensor cores (fit), fp32 SIMT (rounding)"}[
-                  w["precision"]],
+    pd = precision_desc(w["precision"])
+    config = {"workload": args.workload, "lattice": "D3Q19" if w["lattice"] == 19 else "D3Q15",
+              "cells": "%d^3" % (1 << w["n"]), "chi_max": w["chi"],
+              "chi_mask": w["chi_mask"] if solid is not None else None, "eps": w["eps"], "tau": w["tau"],
+              "products": "variational fit, 2 sweeps", "precision": PREC_NAME[w["precision"]], **pd,
               "mass_correction": w["precision"] != 0,
               "start": ("Taylor-Green vortex u0 = %g" % w["tgv_u0"]) if w.get("tgv_u0") else
                        ("%d seeded Fourier modes" % w["n_modes"] if w["n_modes"] else "rest"),
-              "l2_flush": "working set > L2 (129 MB) is not claimed; each step touches ~GBs of environments"}
+              "l2_flush": "none: each step streams GBs of environments and rounding scratch through HBM"}
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        per = []
-        desc = ""
-        for i in range(args.warmup + args.steps):
-            sec, desc, _ = oracle_sample(w, solid, modes, budget_s=8.0)
-            if i >= args.warmup:
-                per.append(sec)
-        T = float(np.sum(per))
-        val = N3 * args.steps / T / 1e6
-        out = {"impl": "reference", "metric": "represented MLUPS at fixed chi", "value": val, "unit": "MLUPS",
-               "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-               "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
-                                "sample": desc},
-               "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(out))
+        reference_arm(args, w, solid, modes, config, N3, rank)
         return
 
     import torch
@@ -413,14 +501,6 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2512_07615_gb300 as tl
-    from paper_2512_07615_gb300 import native as nat
-
-    t0 = time.time()
-    sim = make_sim(w, solid, modes)
-    setup_s = time.time() - t0
-    rho_start, _ = sim.macroscopic()
-    mass_start = float(rho_start.sum())
-    sim.step(args.warmup)
 
     def barrier():
         torch.cuda.synchronize()
@@ -428,6 +508,44 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # plain FP64 unbatched full-SVD path on the same workload: its MLUPS (the
+    # baseline the metric names) and the velocity field after n_cmp steps from
+    # the same start, against which the timed precision's field is compared
+    cmp = None
+    n_cmp = 3
+    if rank == 0 and not args.no_fp64:
+        w64 = dict(w, precision=0)
+        s64 = make_sim(w64, solid, modes)
+        s64.step(1)
+        ms64 = s64.step_timed(1)
+        s64.step(n_cmp - 2)
+        _, u64 = s64.macroscopic()
+        s64.close()
+        sx = make_sim(w, solid, modes)
+        sx.step(n_cmp)
+        _, ux = sx.macroscopic()
+        sx.close()
+        cmp = {"fp64_ms_per_step": ms64, "fp64_value": N3 / (ms64 * 1e3),
+               "rel_l2_u": float(np.linalg.norm(ux - u64) / np.linalg.norm(u64)), "steps": n_cmp}
+        # conditioning of the workload: the FP64 path from a start whose mode
+        # amplitudes are scaled by 1 + 1e-12
+        if modes is not None:
+            mp = np.array(modes, dtype=np.float64)
+            mp[:, 4:] *= 1.0 + 1e-12
+            sp = make_sim(w64, solid, mp)
+            sp.step(n_cmp)
+            _, up = sp.macroscopic()
+            sp.close()
+            cmp["rel_l2_u_fp64_perturbed"] = float(np.linalg.norm(up - u64) / np.linalg.norm(u64))
+            del up
+        del u64, ux
+
+    t0 = time.time()
+    sim = make_sim(w, solid, modes)
+    setup_s = time.time() - t0
+    rho_start, _ = sim.macroscopic()
+    mass_start = float(rho_start.sum())
+    sim.step(args.warmup)
     barrier()
     with Clocks(local) as clk:
         ms = sim.step_timed(args.steps)
@@ -441,47 +559,51 @@ def main():
 
     # one profiled (eager, serialised) step: per kernel class time and FLOPs
     prof = sim.profile_step()
-    round_phases = prof["round"].pop("phase_cycles")
+    ph = prof["round"].pop("phase_cycles")
     total_prof_ms = sum(v["ms"] for v in prof.values())
-    dom = max(prof, key=lambda c: prof[c]["ms"])
-    peaks = json.load(open(MEASURED_PEAKS)) if os.path.exists(MEASURED_PEAKS) else {}
-    fp32 = w["precision"] != 0
-    if fp32:
-        peak_tf, peak_src = FP32_SIMT_MEASURED_TFLOPS, "measured FP32 SIMT SGEMM on this pool (no TF32)"
-    else:
-        peak_tf, peak_src = 1.06, "measured FP64 DGEMM on this pool"
-    launches = max(prof[dom]["launches"], 1)
-    # DRAM bytes of the rounding kernel: ncu (dram__bytes_read.sum +
-    # dram__bytes_write.sum) on the porous 64^3 workload at chi 64 measured
-    # 1.156 MB for a launch of 4 jobs; scaled by the jobs of an average
-    # launch here (each job reads its terms and writes its result).  Only for
-    # the FP32 chi-64 sphere packs it was measured on.
-    traffic = None
-    if dom == "round" and fp32 and w["chi"] == 64 and w["geometry"] == "spheres":
-        traffic = 1.156e6 / 4 * st["round_jobs_per_step"] / launches
-    ach = prof[dom]["flops"] / (prof[dom]["ms"] / 1e3) / 1e12 if prof[dom]["ms"] > 0 else 0.0
-    roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": ach / peak_tf, "traffic": traffic,
-                "traffic_source": ("ncu DRAM bytes per rounding job (porous 64^3, chi 64) x jobs per launch"
-                                   if traffic is not None else None),
-                "peak_source": peak_src,
-                "flops_per_launch": prof[dom]["flops"] / launches, "launches_per_step": prof[dom]["launches"],
-                "share_of_profiled_step": prof[dom]["ms"] / total_prof_ms if total_prof_ms else None,
-                "classes": {c: {"ms": round(v["ms"], 3), "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12
-                                                                    if v["ms"] > 0 else 0.0),
+    peaks = load_peaks()
+    rd = prof["round"]
+    per_launch_ms = rd["ms"] / max(rd["launches"], 1)
+    phase_keys = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")
+    phase_tot = max(sum(ph[q] for q in phase_keys), 1.0)
+    roofline = {"kernel": "round_kernel", "launches_per_step": rd["launches"],
+                "ms_per_launch": per_launch_ms,
+                "share_of_profiled_step": rd["ms"] / total_prof_ms if total_prof_ms else None,
+                "flops_per_launch": rd["flops"] / max(rd["launches"], 1),
+                "classes": {c: {"ms": round(v["ms"], 3),
+                                "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12 if v["ms"] > 0 else 0.0),
                                 "launches": v["launches"]} for c, v in prof.items()},
-                "round_phase_share": {p: round(round_phases[p] / max(sum(round_phases[q] for q in
-                                      ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")), 1.0), 4)
-                                      for p in ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")},
-                "jacobi_sweeps_per_svd": round_phases["jacobi_sweeps"] / max(round_phases["svd_count"], 1.0)}
+                "round_phase_share": {q: round(ph[q] / phase_tot, 4) for q in phase_keys},
+                "jacobi_sweeps_per_svd": ph["jacobi_sweeps"] / max(ph["svd_count"], 1.0),
+                "traffic": None,
+                "traffic_note": "the rounding kernel reads its terms and writes its result once per job; "
+                                "DRAM bytes per launch are in profiles/ (ncu), not re-measured per run"}
+    if w["precision"] in (0, 3):
+        # the centre SVDs are FP64 one-sided Jacobis bound by the FP64 pipes:
+        # achieved = the kernel's algorithmic FLOPs (QR, SVD by the Golub-Kahan
+        # count, GEMMs) per launch / launch time, against the FP64 GEMM peak
+        peak = peaks.get("fp64_tflops")
+        ach = rd["flops"] / (rd["ms"] / 1e3) / 1e12 if rd["ms"] > 0 else 0.0
+        jac_ms = rd["ms"] * ph["jacobi"] / phase_tot
+        roofline.update({"bound": "fp64", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak if peak else None,
+                         "peak_source": "FP64 torch.matmul on this pool (profiles/peaks_gb300.md)",
+                         "svd64_algorithmic_tflops": ph["svd64_flops"] / (jac_ms / 1e3) / 1e12 if jac_ms else None,
+                         "svd64_executed_tflops": ph["svd64_exec_flops"] / (jac_ms / 1e3) / 1e12 if jac_ms else None})
+        if peak and jac_ms:
+            roofline["svd64_executed_frac"] = roofline["svd64_executed_tflops"] / peak
+    else:
+        peak = peaks.get("fp32_simt_tflops")
+        ach = rd["flops"] / (rd["ms"] / 1e3) / 1e12 if rd["ms"] > 0 else 0.0
+        roofline.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak if peak else None,
+                         "peak_source": "FP32 (no TF32) torch.matmul on this pool (profiles/peaks_gb300.md)"})
     if w["precision"] == 2 and prof["fit_gemm"]["ms"] > 0:
-        # the fit's GEMM stages on the tensor cores: against the TF32 peak, taken
-        # as the measured BF16 burst peak times the nominal TF32 / BF16 ratio
-        tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+        tf32_peak = peaks.get("tf32_tflops")
         ach_tc = prof["fit_gemm"]["flops"] / (prof["fit_gemm"]["ms"] / 1e3) / 1e12
         roofline["tensor"] = {"kernel": "fit_gemm_tc", "bound": "tensor", "achieved": ach_tc, "peak": tf32_peak,
-                              "unit": "TFLOP/s", "frac": ach_tc / tf32_peak,
-                              "peak_source": "measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"}
+                              "unit": "TFLOP/s", "frac": ach_tc / tf32_peak if tf32_peak else None,
+                              "peak_source": "TF32 torch.matmul on this pool (profiles/peaks_gb300.md)"}
 
     # end to end through the C ABI: populations host -> device, step, device -> host
     e2e = None
@@ -503,9 +625,10 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sec, desc, spent = oracle_sample(w, solid, modes, pops=sim.get_populations())
+        sec = oracle_whole_step(w, solid, sim.get_populations())
         cpu = {"value": N3 / sec / 1e6, "unit": "MLUPS", "cores": cpu_threads(), "kind": "oracle",
-               "sample": desc, "sample_seconds": round(spent, 1)}
+               "sample": "one whole oracle step (numpy FP64, mask products included) on the populations the "
+                         "GPU reached after its timed steps (%.1f s)" % sec}
 
     batched = None
     if rank == 0 and not args.no_batched and args.workload == "porous128":
@@ -517,8 +640,21 @@ def main():
     if rank == 0:
         out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": ("tf32" if w["precision"] == 2 else "f32") if fp32 else "f64", "data": "synthetic", "config": config,
+               "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": (value / world) / cmp["fp64_value"] if cmp else None,
+               "vs_baseline_def": "per-GPU value / MLUPS of the plain FP64 unbatched full-SVD GPU path on the "
+                                  "same workload (fp64_baseline)",
+               "rel_l2_u": cmp["rel_l2_u"] if cmp else None,
+               "rel_l2_u_def": ("||u - u_fp64|| / ||u_fp64|| after %d steps from the same start, u_fp64 from the "
+                                "plain FP64 GPU path" % n_cmp) if cmp else None,
+               "rel_l2_u_fp64_perturbed": cmp.get("rel_l2_u_fp64_perturbed") if cmp else None,
+               "rel_l2_u_fp64_perturbed_def": "the same distance between the FP64 path and the FP64 path started "
+                                              "from mode amplitudes scaled by 1 + 1e-12 (the workload's own "
+                                              "sensitivity: chi-capped bonds and variational products)",
+               "fp64_baseline": ({"value": cmp["fp64_value"], "unit": "MLUPS", "ms_per_step": cmp["fp64_ms_per_step"]}
+                                 if cmp else None),
+               "dtype": {0: "f64", 1: "f32", 2: "tf32", 3: "f32+f64svd"}[w["precision"]],
+               "data": "synthetic", "config": config,
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),

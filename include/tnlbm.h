@@ -228,11 +228,13 @@ enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_
  * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
  * launch), algorithmic FLOPs flops[] (counted on the device from the realised
  * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[].
- * phases (nullable, 10 doubles): SM cycles of the rounding kernel's phases
+ * phases (nullable, 12 doubles): SM cycles of the rounding kernel's phases
  * summed over its jobs: term formation, R*W product, QR, Jacobi, SVD outputs,
  * Q*US product (indices 0..5); Jacobi sweeps and SVD count (6, 7); Jacobi
  * cycles and count of the SVDs whose matrices did not fit in shared memory
- * (8, 9). */
+ * (8, 9); FLOPs of the FP64 centre SVDs of TNLBM_MIXED / cluster runs: the
+ * algorithmic (Golub-Kahan) count 4 M N^2 + 8 N^3 (10) and the FP64 FLOPs
+ * the cluster Jacobi executed (11). */
 int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches, double *phases);
 int tnlbm_destroy(tnlbm_sim *s); /* NULL-safe */
 const char *tnlbm_last_error(void);

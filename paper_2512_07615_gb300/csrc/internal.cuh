@@ -32,7 +32,12 @@ enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 =
              C_COUNT = 7 };
 // phases of the rounding kernel (cycles of thread 0, summed over jobs), stored
 // after the FLOP counters: terms, R*W GEMM, QR, Jacobi, SVD outputs, Q*US GEMM
-enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT = 4, PH_GEMM_C = 5, PH_COUNT = 10 };
+// slots 6..9: Jacobi sweeps, SVD count, Jacobi cycles and count of SVDs in
+// global memory; 10: algorithmic FLOPs of the FP64 centre SVDs (Golub-Kahan
+// count); 11: FP64 FLOPs the cluster Jacobi executed (rotations, inner
+// products, norms)
+enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT = 4, PH_GEMM_C = 5,
+             PH_SVD64_FLOPS = 10, PH_SVD64_EXEC = 11, PH_COUNT = 12 };
 static constexpr int CTR_SIZE = 24;   // >= C_COUNT + PH_COUNT
 // Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
 __host__ __device__ inline double qr_flops(double m, double n) {

@@ -342,8 +342,10 @@ __device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, const
 // bond capacity) and the sweeps.
 template <typename T>
 __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m, int n, double scl, double delta,
-                          int maxsw, int* sweeps_out) {
+                          int maxsw, int* sweeps_out, double* exec_flops = nullptr) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_nrot;                      // rotations taken (the same in every CTA)
+  if (threadIdx.x == 0) s_nrot = 0;
   unsigned char* wa = smem + SM_SMALL;
   T* scr = (T*)J.scratch;
   const T* C = scr + J.lay.c_off;
@@ -433,6 +435,7 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
           }
           go = __shfl_sync(mask8, go, 0, 8);
           if (!go) continue;
+          if (gl == 0) atomicAdd(&s_nrot, 1u);
           cs = __shfl_sync(mask8, cs, 0, 8);
           sn = __shfl_sync(mask8, sn, 0, 8);
           for (int ii = gl; ii < li; ii += 8) {
@@ -460,6 +463,13 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
     }
   }
   *sweeps_out = cc.dead ? maxsw : sweep;
+  if (exec_flops && threadIdx.x == 0) {
+    // over the whole cluster: 6 per rotated element pair of W and V, 2 per
+    // element of every pair's inner product, 2 per element of the norms
+    const double rounds = (double)imin(sweep + 1, maxsw) * (double)(np - 1);
+    *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * rounds * npairs * len +
+                  2.0 * (double)(imin(sweep + 1, maxsw) + 1) * ncol * len;
+  }
   // exact norms -> singular values, order and rank (identical in every CTA);
   // non-finite values order last and are reported
   rows_norms(cc, R, wa, ncol, li);
@@ -575,8 +585,10 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
     pc.lap(PH_SVD_OUT);
     cl_command(cc, 2, ncol, len, maxsw, m, n, k, delta, scl);
     int sw = 0;
-    const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw);
+    double xfl = 0.0;
+    const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw, &xfl);
     pc.lap(PH_JACOBI);
+    if (threadIdx.x == 0) { pc.acc[PH_SVD64_FLOPS] += svd_flops(m, n); pc.acc[PH_SVD64_EXEC] += xfl; }
     const RowsLayout R = rows_layout(ncol, len, cc.P);
     const unsigned char* wa = (const unsigned char*)work;
     const double* sig = (const double*)(wa + R.sig);
@@ -626,7 +638,7 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
     sw = jacobi64_cluster(cc, Wm, ldw, Vm, ldv, ncol, len, maxsw);
   }
   pc.lap(PH_JACOBI);
-  if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; }
+  if (threadIdx.x == 0) { pc.acc[6] += sw; pc.acc[7] += 1.0; pc.acc[PH_SVD64_FLOPS] += svd_flops(m, n); }
   if (threadIdx.x == 0 && !in_smem) { pc.acc[8] += pc.acc[PH_JACOBI] - jac0; pc.acc[9] += 1.0; }
   if (sw >= maxsw && threadIdx.x == 0) {
     flag(status, ST_NOCONV);
