@@ -657,6 +657,8 @@ def main():
                "data": "synthetic", "config": config,
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
+               "rounding_launch": {"jobs_per_step": st["round_jobs_per_step"], "ctas_per_step": st["round_ctas_per_step"],
+                                   "max_cluster": st["max_cluster"]},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
                "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

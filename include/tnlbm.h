@@ -149,9 +149,9 @@ typedef struct {
                               TNLBM_E_TIMEOUT (the simulation can be destroyed) */
   int max_cluster;         /* CTAs per rounding job for the FP64 centre SVDs
                               (TNLBM_MIXED and TNLBM_FP64): 0 = automatic (the
-                              largest of 16, 8, 4, 2 at which every job of a
+                              largest size <= 16 at which every job of a
                               dependency level is resident at once), 1 = one
-                              CTA per job, else a cap (power of two <= 16)      */
+                              CTA per job, else a cap (<= 16)                   */
 } tnlbm_config;
 
 enum { TNLBM_FACE_WALL = 0, TNLBM_FACE_VELOCITY = 1, TNLBM_FACE_PRESSURE = 2 };
@@ -165,7 +165,7 @@ typedef struct {
   double rho0;               /* last mean density rho_0 (Sec. 3.2)               */
   int status;                /* device status word (0 = fine)                    */
   int gpu_launches_per_step; /* kernels launched by one tnlbm_step(1)            */
-  int round_jobs_per_step;   /* rounding jobs (one CTA each) in one step         */
+  int round_jobs_per_step;   /* rounding jobs in one step                       */
   int product_jobs_per_step; /* fit or zip-up product jobs in one step           */
   double mass;               /* sum of rho over all cells at the last rho_0 node
                                 (rho_0 * N_fluid)                                */
@@ -173,6 +173,10 @@ typedef struct {
                                 squared norm discarded at each truncation
                                 (Eq. svd-move tails); difference two calls for
                                 a step's share                                  */
+  int round_ctas_per_step;   /* CTAs of all rounding launches of one step (a job
+                                runs on a cluster of CTAs when its centre SVDs
+                                are FP64)                                       */
+  int max_cluster;           /* largest cluster of a rounding launch            */
 } tnlbm_stats;
 
 /* Build a simulation: shift MPOs, mask MPS, initial populations, and a CUDA
@@ -228,13 +232,15 @@ enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_
  * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
  * launch), algorithmic FLOPs flops[] (counted on the device from the realised
  * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[].
- * phases (nullable, 12 doubles): SM cycles of the rounding kernel's phases
+ * phases (nullable, 17 doubles): SM cycles of the rounding kernel's phases
  * summed over its jobs: term formation, R*W product, QR, Jacobi, SVD outputs,
  * Q*US product (indices 0..5); Jacobi sweeps and SVD count (6, 7); Jacobi
  * cycles and count of the SVDs whose matrices did not fit in shared memory
  * (8, 9); FLOPs of the FP64 centre SVDs of TNLBM_MIXED / cluster runs: the
  * algorithmic (Golub-Kahan) count 4 M N^2 + 8 N^3 (10) and the FP64 FLOPs
- * the cluster Jacobi executed (11). */
+ * the cluster Jacobi executed (11); cycles of the cluster Jacobi (leader CTA)
+ * in the column norms, forming and sending the pair inner products, waiting
+ * for the other CTAs' parts, the rotation angles and the rotations (12..16). */
 int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches, double *phases);
 int tnlbm_destroy(tnlbm_sim *s); /* NULL-safe */
 const char *tnlbm_last_error(void);

@@ -940,9 +940,8 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
     set_error("bad precision");
     return TNLBM_E_ARG;
   }
-  if (C.jacobi_max_sweeps < 0 || C.wait_limit_ns < 0 || C.max_cluster < 0 || C.max_cluster > 16 ||
-      (C.max_cluster & (C.max_cluster - 1)) != 0) {
-    set_error("jacobi_max_sweeps, wait_limit_ns >= 0; max_cluster 0 or a power of two <= 16");
+  if (C.jacobi_max_sweeps < 0 || C.wait_limit_ns < 0 || C.max_cluster < 0 || C.max_cluster > 16) {
+    set_error("jacobi_max_sweeps, wait_limit_ns >= 0; max_cluster in 0..16");
     return TNLBM_E_ARG;
   }
   if (C.learned_rank != 0 && C.learned_rank != 1 && C.learned_rank != 3) {
@@ -1185,9 +1184,13 @@ int tnlbm_stats_get(tnlbm_sim* s, tnlbm_stats* out) {
   out->mass = scal[SC_RHO0] * s->n_fluid;
   out->round_jobs_per_step = 0;
   out->product_jobs_per_step = 0;
+  out->round_ctas_per_step = 0;
+  out->max_cluster = 1;
   for (auto& lv : s->levels) {
     out->round_jobs_per_step += (int)lv.rj.size();
     out->product_jobs_per_step += (int)(lv.fj.size() + lv.zj.size());
+    out->round_ctas_per_step += (int)lv.rj.size() * lv.cluster;
+    out->max_cluster = std::max(out->max_cluster, lv.cluster);
   }
   return 0;
 }

@@ -39,6 +39,7 @@ struct ClusterCmd {
 struct __align__(16) ClusterShared {
   unsigned long long bar[2];   // work barriers (alternating)
   unsigned long long bar_exit; // exit barrier
+  unsigned long long xbar[2];  // data exchanges (alternating): one local arrival + the bytes expected
   ClusterCmd cmd;
   int flags[2][CL_MAX];        // per-sweep "rotated" flags of every CTA (double buffered)
   int peer_dead;               // set by a CTA of the cluster that gave up waiting
@@ -49,6 +50,7 @@ struct ClusterCtx {
   ClusterShared* sh;           // this CTA's block (same offset in every CTA)
   int P, rank;
   unsigned nb;                 // work barriers passed so far
+  unsigned xe;                 // data exchanges completed so far
   bool dead;                   // a wait ran out
   long long limit_ns;          // wait limit of the work barriers
   int* status;
@@ -118,6 +120,7 @@ __device__ inline void cl_init(ClusterCtx& c, ClusterShared* sh, int* status, lo
   c.P = (int)cl_size();
   c.rank = (int)cl_rank();
   c.nb = 0;
+  c.xe = 0;
   c.dead = false;
   c.limit_ns = limit_ns;
   c.status = status;
@@ -126,6 +129,8 @@ __device__ inline void cl_init(ClusterCtx& c, ClusterShared* sh, int* status, lo
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh->bar[0])), "r"(c.P));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh->bar[1])), "r"(c.P));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh->bar_exit)), "r"(c.P));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh->xbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sh->xbar[1])), "r"(1));
     sh->cmd.op = 0;
     sh->peer_dead = 0;
     for (int i = 0; i < 2 * CL_MAX; ++i) (&sh->flags[0][0])[i] = 0;
@@ -181,6 +186,58 @@ __device__ inline void cl_exit(ClusterCtx& c) {
   if (threadIdx.x < (unsigned)c.P) cl_arrive_remote(&c.sh->bar_exit, threadIdx.x);
   const bool ok = cl_poll(&c.sh->bar_exit, 0, 30000000000LL);
   if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(c.status, ST_TIMEOUT);
+}
+
+// ---------------------------------------------------------------- data exchanges
+// An exchange sends every CTA the same number of bytes from every CTA of the
+// cluster with st.async, each store completing its bytes on the receiver's
+// exchange mbarrier; the receiver's one arrival announces the total it
+// expects.  The arrival of the data is the synchronisation: a CTA that has all
+// bytes of exchange e knows every CTA finished the work before it sent, and
+// nobody sends exchange e + 2 into the same buffer before it has this CTA's
+// exchange e + 1, which it sends only after reading exchange e.
+
+// Announce the bytes of this exchange (thread 0; before this CTA's own sends).
+__device__ inline void cl_xchg_expect(ClusterCtx& c, unsigned bytes) {
+  if (c.P > 1 && !c.dead && threadIdx.x == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&c.sh->xbar[c.xe & 1])),
+                 "r"(bytes) : "memory");
+}
+
+// One double into CTA `rank`'s copy of *p, counted on its current exchange.
+__device__ __forceinline__ void cl_xchg_send(const ClusterCtx& c, const double* p, unsigned rank, double v) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               ::"r"(cl_map(p, rank)), "l"(__double_as_longlong(v)), "r"(cl_map(&c.sh->xbar[c.xe & 1], rank))
+               : "memory");
+}
+
+// Wait (thread 0 polls, bounded by the wait limit in SM clocks) until all
+// bytes of this exchange have arrived; then the CTA meets.  False (uniformly)
+// once this CTA has given up.
+__device__ inline bool cl_xchg_wait(ClusterCtx& c) {
+  if (c.P == 1) {
+    __syncthreads();
+    return true;
+  }
+  const unsigned j = c.xe & 1, parity = (c.xe >> 1) & 1;
+  ++c.xe;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (!c.dead && !cl_try_wait(&c.sh->xbar[j], parity)) {
+      const long long t0 = clock64(), lim = 2 * c.limit_ns;     // ~1 cycle per 0.5 ns
+      while (!cl_try_wait(&c.sh->xbar[j], parity))
+        if (clock64() - t0 > lim) { ok = 0; break; }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (!c.dead && !s_ok) {
+    c.dead = true;
+    if (threadIdx.x == 0) atomicOr(c.status, ST_TIMEOUT);
+    if (threadIdx.x < (unsigned)c.P) cl_store_remote(&c.sh->peer_dead, threadIdx.x, 1);
+  }
+  return !c.dead;
 }
 
 // Leader: write a command into every worker's shared memory, then meet them.

@@ -35,9 +35,12 @@ enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 =
 // slots 6..9: Jacobi sweeps, SVD count, Jacobi cycles and count of SVDs in
 // global memory; 10: algorithmic FLOPs of the FP64 centre SVDs (Golub-Kahan
 // count); 11: FP64 FLOPs the cluster Jacobi executed (rotations, inner
-// products, norms)
+// products, norms); 12..16: cycles of the leader's cluster Jacobi spent in
+// the column norms (with their exchange), forming and sending the pair inner
+// products, waiting for the other CTAs' parts, the angles, and the rotations
 enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT = 4, PH_GEMM_C = 5,
-             PH_SVD64_FLOPS = 10, PH_SVD64_EXEC = 11, PH_COUNT = 12 };
+             PH_SVD64_FLOPS = 10, PH_SVD64_EXEC = 11, PH_RX_NORM = 12, PH_RX_DOT = 13, PH_RX_WAIT = 14,
+             PH_RX_ANGLE = 15, PH_RX_ROT = 16, PH_COUNT = 17 };
 static constexpr int CTR_SIZE = 24;   // >= C_COUNT + PH_COUNT
 // Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
 __host__ __device__ inline double qr_flops(double m, double n) {
@@ -207,8 +210,8 @@ void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits,
                   int cluster = 1);
 size_t round_smem_bytes();
 // CTAs per job for a launch of njobs rounding jobs whose centre SVDs run in
-// FP64: the largest cluster size (<= cap, power of two, <= 16) at which all
-// njobs clusters are resident at once on the current device; 1 if none.
+// FP64: the largest cluster size (<= cap, <= 16) at which all njobs clusters
+// are resident at once on the current device; 1 if none.
 template <typename T>
 int round_cluster_size(int njobs, int cap);
 // increments the device step counter read by the rank model

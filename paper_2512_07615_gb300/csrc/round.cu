@@ -216,14 +216,31 @@ struct PhaseClock {
   }
 };
 
+// Lap timer of the cluster Jacobi's sub-phases (thread 0 of the leader CTA;
+// acc null elsewhere).
+struct RxClock {
+  double* acc;
+  long long t0;
+  __device__ explicit RxClock(double* a) : acc(threadIdx.x == 0 ? a : nullptr), t0(0) {
+    if (acc) t0 = clock64();
+  }
+  __device__ void lap(int ph) {
+    if (!acc) return;
+    const long long t = clock64();
+    acc[ph] += (double)(t - t0);
+    t0 = t;
+  }
+};
+
 // ---------------------------------------------------------------- row-partitioned FP64 SVD
 // Work-area layout (bytes, same in every CTA of the cluster) of svd64_rows:
-// the CTA's rows of W and V, the column norms, per-pair rotations, the
-// exchange buffers of the pair inner products and of the column norms, and
-// the singular values / order / tails the rank rule reads.
+// the CTA's rows of W and V (doubles; the FP32 phase keeps its rows in the
+// first halves), the column norms, the exchange buffers of the pair inner
+// products and of the column norms, and the singular values / order / tails
+// the rank rule reads.
 struct RowsLayout {
   int lw, lv, npairs;
-  size_t wl, vl, nrm, pc, ps, pf, xb, nbuf, sig, perm, tail, total;
+  size_t wl, vl, nrm, pc, ps, pf, gl, xb, nbuf, sig, perm, tail, total;
 };
 __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
   RowsLayout R;
@@ -238,6 +255,7 @@ __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
   R.pc = take((size_t)R.npairs * 8);
   R.ps = take((size_t)R.npairs * 8);
   R.pf = take((size_t)R.npairs * 4);
+  R.gl = take((size_t)imax(R.npairs, ncol) * 8);
   R.xb = take((size_t)2 * R.npairs * P * 8);
   R.nbuf = take((size_t)ncol * P * 8);
   R.sig = take((size_t)ncol * 8);
@@ -247,6 +265,22 @@ __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
   return R;
 }
 
+// Sum of n doubles x[0], x[s], x[2s], ... in a fixed order with four
+// independent accumulators (a short dependency chain on the FP64 pipe); the
+// same inputs give the same double in every CTA.
+__device__ __forceinline__ double sum4(const double* x, int n, int s) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int c = 0;
+  for (; c + 3 < n; c += 4) {
+    a0 += x[(size_t)c * s];
+    a1 += x[(size_t)(c + 1) * s];
+    a2 += x[(size_t)(c + 2) * s];
+    a3 += x[(size_t)(c + 3) * s];
+  }
+  for (; c < n; ++c) a0 += x[(size_t)c * s];
+  return (a0 + a1) + (a2 + a3);
+}
+
 // round-robin pair p of round rnd over np (even) indices, a < b
 __device__ __forceinline__ void rr_pair(int rnd, int p, int np, int& a, int& b) {
   if (p == 0) { a = rnd; b = np - 1; }
@@ -254,68 +288,220 @@ __device__ __forceinline__ void rr_pair(int rnd, int p, int np, int& a, int& b) 
   if (a > b) { const int t = a; a = b; b = t; }
 }
 
-// Column norms of W over the cluster: every CTA adds its rows, sends the
-// partial sums to every CTA, and sums them in rank order (the same order, so
-// the same doubles, in every CTA).  Ends with nrm[] valid everywhere.
-__device__ inline void rows_norms(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, int ncol, int li) {
-  const double* Wl = (const double*)(wa + R.wl);
+// Column norms of W over the cluster: every CTA adds its rows (FP64 sums of
+// its S-typed entries), sends the partial sums to every CTA, and sums them in
+// rank order (the same order, so the same doubles, in every CTA).  Ends with
+// nrm[] valid everywhere.
+template <typename S>
+__device__ inline void rows_norms(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, const S* Wl, int ncol,
+                                  int li) {
+  // FP64 work goes one instruction per warp at a time whatever the active
+  // lanes, so every FP64 step here runs one thread per column, all lanes busy
   double* nb = (double*)(wa + R.nbuf);
   double* nrm = (double*)(wa + R.nrm);
-  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
-  const unsigned mask8 = 0xffu << (threadIdx.x & 24);
-  // stores into the other CTAs follow the last cluster barrier by at most a
-  // round, far less than a CTA that gave up waits at the exit barrier
-  const bool alive = !cc.dead;
-  for (int j0 = 0; j0 < ncol; j0 += ngrp) {
-    const int j = j0 + grp;
-    double v = 0.0;
-    if (j < ncol)
-      for (int ii = gl; ii < li; ii += 8) { const double x = Wl[(size_t)j * R.lw + ii]; v += x * x; }
-    v += __shfl_xor_sync(mask8, v, 4, 8);
-    v += __shfl_xor_sync(mask8, v, 2, 8);
-    v += __shfl_xor_sync(mask8, v, 1, 8);
-    if (j < ncol) {
-      if (cc.P == 1) { if (gl == 0) nb[j] = v; }
-      else if (alive)
-        for (int d = gl; d < cc.P; d += 8) cl_store_remote(nb + (size_t)j * cc.P + cc.rank, d, v);
-    }
-  }
-  cl_sync(cc);
+  double* loc = (double*)(wa + R.gl);
+  cl_xchg_expect(cc, (unsigned)(ncol * cc.P * 8));
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
-    double a = 0.0;
-    for (int c = 0; c < cc.P; ++c) a += nb[(size_t)j * cc.P + c];
-    nrm[j] = a;
+    const S* w = Wl + (size_t)j * R.lw;
+    double v0 = 0.0, v1 = 0.0;
+    int ii = 0;
+    for (; ii + 1 < li; ii += 2) {
+      const double x0 = (double)w[ii], x1 = (double)w[ii + 1];
+      v0 += x0 * x0;
+      v1 += x1 * x1;
+    }
+    if (ii < li) { const double x0 = (double)w[ii]; v0 += x0 * x0; }
+    const double v = v0 + v1;
+    if (cc.P == 1) nb[j] = v;
+    else loc[j] = v;
   }
+  // stores into the other CTAs follow the last exchange by at most a round,
+  // far less than a CTA that gave up waits at the exit barrier
+  if (cc.P > 1) {
+    __syncthreads();
+    if (!cc.dead)
+      for (int idx = threadIdx.x; idx < ncol * cc.P; idx += blockDim.x) {
+        const int j = idx / cc.P, d = idx % cc.P;
+        cl_xchg_send(cc, nb + (size_t)j * cc.P + cc.rank, d, loc[j]);
+      }
+  }
+  cl_xchg_wait(cc);
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) nrm[j] = sum4(nb + (size_t)j * cc.P, cc.P, 1);
   __syncthreads();
 }
 
-// This CTA's parts of the inner products of every pair of round rnd, sent to
-// every CTA's exchange slots xq[p][rank]; then the cluster barrier.
-__device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, const double* Wl, double* xq, int rnd,
-                                      int np, int ncol, int li) {
+// This CTA's parts of the inner products of every pair of round rnd (FP64
+// sums), sent to every CTA's exchange slots xq[p][rank]; then the cluster
+// barrier.
+template <typename S>
+__device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, const S* Wl,
+                                      double* xq, int rnd, int np, int ncol, int li, RxClock& rx) {
   const int npairs = np / 2;
-  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
-  const unsigned mask8 = 0xffu << (threadIdx.x & 24);
-  const bool alive = !cc.dead;
-  for (int p0 = 0; p0 < npairs; p0 += ngrp) {
-    const int p = p0 + grp;
+  double* loc = (double*)(wa + R.gl);
+  cl_xchg_expect(cc, (unsigned)(npairs * cc.P * 8));
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    int a, b;
+    rr_pair(rnd, p, np, a, b);
     double g = 0.0;
-    if (p < npairs) {
-      int a, b;
-      rr_pair(rnd, p, np, a, b);
-      if (b < ncol)
-        for (int ii = gl; ii < li; ii += 8) g += Wl[(size_t)a * R.lw + ii] * Wl[(size_t)b * R.lw + ii];
+    if (b < ncol) {
+      const S* wa_ = Wl + (size_t)a * R.lw;
+      const S* wb_ = Wl + (size_t)b * R.lw;
+      double g0 = 0.0, g1 = 0.0;
+      int ii = 0;
+      for (; ii + 1 < li; ii += 2) {
+        g0 += (double)wa_[ii] * (double)wb_[ii];
+        g1 += (double)wa_[ii + 1] * (double)wb_[ii + 1];
+      }
+      if (ii < li) g0 += (double)wa_[ii] * (double)wb_[ii];
+      g = g0 + g1;
     }
-    g += __shfl_xor_sync(mask8, g, 4, 8);
-    g += __shfl_xor_sync(mask8, g, 2, 8);
-    g += __shfl_xor_sync(mask8, g, 1, 8);
-    if (p < npairs) {
-      if (cc.P == 1) { if (gl == 0) xq[p] = g; }
-      else if (alive)
-        for (int d = gl; d < cc.P; d += 8) cl_store_remote(xq + (size_t)p * cc.P + cc.rank, d, g);
-    }
+    if (cc.P == 1) xq[p] = g;
+    else loc[p] = g;
   }
-  return cl_sync(cc);
+  if (cc.P > 1) {
+    __syncthreads();
+    if (!cc.dead)
+      for (int idx = threadIdx.x; idx < npairs * cc.P; idx += blockDim.x) {
+        const int p = idx / cc.P, d = idx % cc.P;
+        cl_xchg_send(cc, xq + (size_t)p * cc.P + cc.rank, d, loc[p]);
+      }
+  }
+  rx.lap(PH_RX_DOT);
+  const bool ok = cl_xchg_wait(cc);
+  rx.lap(PH_RX_WAIT);
+  return ok;
+}
+
+// Rotation of a pair with norms al, be and inner product g (all exchanged
+// FP64 values, identical in every CTA), for rows of type S: false if the pair
+// counts as orthogonal (g^2 <= tol2 al be) or a column is negligible.
+// t = tan(theta) is Rutishauser's root, evaluated in FP32 (for |zeta| > 1e18,
+// a column near zero against a large one, t = 1 / (2 zeta) in FP64, where the
+// FP32 quotient would overflow).  FP64 rows: c = (1 + t^2)^(-1/2) by two FP64
+// Newton steps from the FP32 value and s = c t, so the rotation is orthogonal
+// to FP64 accuracy and an angle off by FP32 round-off only leaves a residual
+// the next sweep removes.  FP32 rows: c, s in FP32.  The new norms are
+// al - t g and be + t g (exact for the exact root; recomputed every sweep).
+template <typename S>
+__device__ __forceinline__ bool rows_angle(double al, double be, double g, double tol2, S& cs, S& sn,
+                                           double& na, double& nb) {
+  const double amin = sizeof(S) == 8 ? 1e-250 : 1e-60;
+  if (g == 0.0 || !(al > amin) || !(be > amin) || g * g <= tol2 * al * be) return false;
+  const double zd = (be - al) / (2.0 * g);
+  double t;
+  if (fabs(zd) > 1e18) {
+    t = 0.5 / zd;
+  } else {
+    const float zeta = (float)zd;
+    const float az = fabsf(zeta);
+    t = (double)copysignf(1.f / (az + sqrtf(1.f + zeta * zeta)), zeta);
+  }
+  double c, s;
+  if constexpr (sizeof(S) == 8) {
+    const double x = 1.0 + t * t;
+    c = (double)rsqrtf((float)x);
+    // two Newton steps from the FP32 estimate (relative error 2^-23 -> ~1e-14
+    // -> rounding): the rotation is orthogonal to FP64 rounding, so the
+    // thousands of rotations of one SVD do not drift the column scales
+    c = c * (1.5 - 0.5 * x * c * c);
+    c = c * (1.5 - 0.5 * x * c * c);
+    s = c * t;
+  } else {
+    const float tf = (float)t;
+    if (tf == 0.f) return false;                      // below the FP32 range: nothing to rotate
+    const float cf = 1.f / sqrtf(1.f + tf * tf);
+    c = (double)cf;
+    s = (double)(cf * tf);
+  }
+  cs = (S)c;
+  sn = (S)s;
+  na = al - t * g;                                    // the rotated norms (recomputed every sweep)
+  nb = be + t * g;
+  return true;
+}
+
+// Jacobi sweeps of the row-partitioned matrices (rows of type S) until a sweep
+// rotates nothing or maxsw sweeps; nrot counts rotations.  Returns the sweeps
+// used.
+template <typename S>
+__device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, S* Wl, S* Vl, int ncol,
+                           int li, int vi, int maxsw, double tol2, unsigned* nrot, double* phase_acc) {
+  RxClock rx(phase_acc);
+  unsigned q = 0;                                  // rounds so far (exchange buffer parity)
+  double* nrm = (double*)(wa + R.nrm);
+  double* xb = (double*)(wa + R.xb);
+  S* pcs = (S*)(wa + R.pc);
+  S* psn = (S*)(wa + R.ps);
+  int* pfl = (int*)(wa + R.pf);
+  const int np = (ncol + 1) & ~1, npairs = np / 2;
+  int sweep = 0;
+  if (ncol < 2) return 0;
+  for (; sweep < maxsw; ++sweep) {
+    rows_norms<S>(cc, R, wa, Wl, ncol, li);
+    rx.lap(PH_RX_NORM);
+    int any = 0;
+    bool ok = rows_pair_dots<S>(cc, R, wa, Wl, xb + (size_t)(q & 1) * npairs * cc.P, 0, np, ncol, li, rx);
+    for (int rnd = 0; rnd < np - 1 && ok; ++rnd, ++q) {
+      const double* xq = xb + (size_t)(q & 1) * npairs * cc.P;
+      // one thread per pair: gamma as the partials summed in rank order (the
+      // same doubles in every CTA), the angle and the new norms
+      int rot = 0;
+      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        int a, b;
+        rr_pair(rnd, p, np, a, b);
+        int go = 0;
+        if (b < ncol) {
+          const double g = sum4(xq + (size_t)p * cc.P, cc.P, 1);
+          S cs, sn;
+          double na, nb;
+          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cs, sn, na, nb)) {
+            nrm[a] = na;
+            nrm[b] = nb;
+            pcs[p] = cs;
+            psn[p] = sn;
+            go = 1;
+            atomicAdd(nrot, 1u);
+          }
+        }
+        pfl[p] = go;
+        rot |= go;
+      }
+      any |= __syncthreads_or(rot);
+      rx.lap(PH_RX_ANGLE);
+      // the rotations, one element pair per thread
+      for (int idx = threadIdx.x; idx < npairs * li; idx += blockDim.x) {
+        const int p = idx / li, ii = idx % li;
+        if (!pfl[p]) continue;
+        int a, b;
+        rr_pair(rnd, p, np, a, b);
+        const S cs = pcs[p], sn = psn[p];
+        S* pa = Wl + (size_t)a * R.lw + ii;
+        S* pb = Wl + (size_t)b * R.lw + ii;
+        const S u = *pa, w = *pb;
+        *pa = cs * u - sn * w;
+        *pb = sn * u + cs * w;
+      }
+      for (int idx = threadIdx.x; idx < npairs * vi; idx += blockDim.x) {
+        const int p = idx / vi, ii = idx % vi;
+        if (!pfl[p]) continue;
+        int a, b;
+        rr_pair(rnd, p, np, a, b);
+        const S cs = pcs[p], sn = psn[p];
+        S* pa = Vl + (size_t)a * R.lv + ii;
+        S* pb = Vl + (size_t)b * R.lv + ii;
+        const S u = *pa, w = *pb;
+        *pa = cs * u - sn * w;
+        *pb = sn * u + cs * w;
+      }
+      __syncthreads();
+      rx.lap(PH_RX_ROT);
+      if (rnd + 1 < np - 1)
+        ok = rows_pair_dots<S>(cc, R, wa, Wl, xb + (size_t)((q + 1) & 1) * npairs * cc.P, rnd + 1, np, ncol, li,
+                               rx);
+    }
+    if (!any || cc.dead) break;
+  }
+  return cc.dead ? maxsw : sweep;
 }
 
 // FP64 one-sided Jacobi SVD of the centre matrix C (m x n, T, global) with the
@@ -324,27 +510,22 @@ __device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, const
 // accumulates the rotations.  CTA c owns entries [c len / P, (c+1) len / P)
 // of every column of W and [c ncol / P, (c+1) ncol / P) of every column of V.
 // Per round of the round-robin tournament each CTA forms its parts of the
-// pair inner products gamma, all CTAs exchange them (shared::cluster stores,
-// one cluster barrier) and sum them in rank order, so every CTA takes the same
-// rotations and applies them to its rows.  A pair rotates unless gamma^2 <=
-// tol^2 alpha beta (tol = 16 eps sqrt(len), as the single-CTA Jacobi); its
-// angle t = tan(theta) is Rutishauser's, evaluated in FP32 (in FP64 where
-// |zeta| > 1e18), and the rotation
-// itself is orthogonal to FP64 accuracy (c = (1 + t^2)^(-1/2) by two FP64
-// Newton steps from the FP32 value, s = c t), so W and V stay exactly
-// rotated while an angle that is off by FP32 round-off only leaves a residual
-// the next sweeps remove.  Column norms follow the rotations exactly
-// (c^2 alpha - 2cs gamma + s^2 beta) and are recomputed at the start of every
-// sweep and at the end.  Every CTA then finds the same singular values, order
-// and kept rank (the rank rule of Eq. svd-move with delta) and writes its rows
-// of core k (V^T[:r], r x n) and of U S (m x r).  Called by all threads of
-// every CTA with equal arguments; returns the kept rank (0 if it exceeds the
-// bond capacity) and the sweeps.
+// pair inner products gamma, all CTAs exchange them through distributed
+// shared memory and sum them in rank order, so every CTA takes the same
+// rotations and applies them to its rows; the stopping rule is the
+// single-CTA Jacobi's (16 eps_64 sqrt(len)).  Column norms are recomputed
+// exactly at the start of every sweep and at the end.  Every CTA then finds the
+// same singular values, order and kept rank (the rank rule of Eq. svd-move
+// with delta) and writes its rows of core k (V^T[:r], r x n) and of U S
+// (m x r).  Called by all threads of every CTA with equal arguments; returns
+// the kept rank (0 if it exceeds the bond capacity), the sweeps, whether the
+// sweep limit was reached, and the FP64 FLOPs executed.
 template <typename T>
 __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m, int n, double scl, double delta,
-                          int maxsw, int* sweeps_out, double* exec_flops = nullptr) {
+                          int maxsw, int* sweeps_out, bool* noconv, double* exec_flops = nullptr,
+                          double* phase_acc = nullptr) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ unsigned s_nrot;                      // rotations taken (the same in every CTA)
+  __shared__ unsigned s_nrot;
   if (threadIdx.x == 0) s_nrot = 0;
   unsigned char* wa = smem + SM_SMALL;
   T* scr = (T*)J.scratch;
@@ -357,7 +538,6 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
   double* Wl = (double*)(wa + R.wl);
   double* Vl = (double*)(wa + R.vl);
   double* nrm = (double*)(wa + R.nrm);
-  double* xb = (double*)(wa + R.xb);
   double* sig = (double*)(wa + R.sig);
   int* perm = (int*)(wa + R.perm);
   double* tail = (double*)(wa + R.tail);
@@ -374,105 +554,22 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
     Vl[(size_t)j * R.lv + ii] = (j == v0 + ii) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int np = (ncol + 1) & ~1, npairs = np / 2;
-  const double tol = 16.0 * 2.220446049250313e-16 * sqrt((double)len);
-  const double tol2 = tol * tol;
-  const int gl = threadIdx.x & 7, grp = threadIdx.x >> 3, ngrp = blockDim.x >> 3;
-  int sweep = 0;
-  unsigned q = 0;                                  // rounds so far (exchange buffer parity)
-  if (ncol >= 2) {
-    for (; sweep < maxsw; ++sweep) {
-      rows_norms(cc, R, wa, ncol, li);
-      int rot = 0;
-      bool ok = rows_pair_dots(cc, R, Wl, xb + (size_t)(q & 1) * npairs * cc.P, 0, np, ncol, li);
-      for (int rnd = 0; rnd < np - 1 && ok; ++rnd, ++q) {
-        const double* xq = xb + (size_t)(q & 1) * npairs * cc.P;
-        // a group of 8 lanes per pair: the same sum, angle and rotation in
-        // every CTA.  Lane l adds the partials of CTAs l, l + 8 (in that order)
-        // and the lanes' sums are combined by a fixed xor tree, so every CTA
-        // forms gamma identically; lane 0 takes the angle and the new norms,
-        // the group rotates.
-        for (int p0 = 0; p0 < npairs; p0 += ngrp) {
-          const int p = p0 + grp;
-          const unsigned mask8 = 0xffu << (threadIdx.x & 24);
-          int a = 0, b = ncol;
-          double g = 0.0;
-          if (p < npairs) {
-            rr_pair(rnd, p, np, a, b);
-            for (int c = gl; c < cc.P; c += 8) g += xq[(size_t)p * cc.P + c];
-          }
-          g += __shfl_xor_sync(mask8, g, 4, 8);
-          g += __shfl_xor_sync(mask8, g, 2, 8);
-          g += __shfl_xor_sync(mask8, g, 1, 8);
-          if (p >= npairs || b >= ncol) continue;
-          double cs = 1.0, sn = 0.0;
-          int go = 0;
-          if (gl == 0) {
-            const double al = nrm[a], be = nrm[b];
-            if (g != 0.0 && al > 1e-250 && be > 1e-250 && g * g > tol2 * al * be) {
-              // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); for |zeta| > 1e18 (a
-              // column near zero against a large one) t = 1 / (2 zeta) in FP64,
-              // where the FP32 quotient would overflow and stall the rotation at 0
-              const double zd = (be - al) / (2.0 * g);
-              double t;
-              if (fabs(zd) > 1e18) {
-                t = 0.5 / zd;
-              } else {
-                const float zeta = (float)zd;
-                const float az = fabsf(zeta);
-                t = (double)copysignf(1.f / (az + sqrtf(1.f + zeta * zeta)), zeta);
-              }
-              const double x = 1.0 + t * t;
-              cs = (double)rsqrtf((float)x);
-              cs = cs * (1.5 - 0.5 * x * cs * cs);
-              cs = cs * (1.5 - 0.5 * x * cs * cs);
-              sn = cs * t;
-              const double c2 = cs * cs, s2 = sn * sn, csg = 2.0 * cs * sn * g;
-              nrm[a] = c2 * al - csg + s2 * be;
-              nrm[b] = s2 * al + csg + c2 * be;
-              go = 1;
-            }
-          }
-          go = __shfl_sync(mask8, go, 0, 8);
-          if (!go) continue;
-          if (gl == 0) atomicAdd(&s_nrot, 1u);
-          cs = __shfl_sync(mask8, cs, 0, 8);
-          sn = __shfl_sync(mask8, sn, 0, 8);
-          for (int ii = gl; ii < li; ii += 8) {
-            double* pa = Wl + (size_t)a * R.lw + ii;
-            double* pb = Wl + (size_t)b * R.lw + ii;
-            const double u = *pa, w = *pb;
-            *pa = cs * u - sn * w;
-            *pb = sn * u + cs * w;
-          }
-          for (int ii = gl; ii < vi; ii += 8) {
-            double* pa = Vl + (size_t)a * R.lv + ii;
-            double* pb = Vl + (size_t)b * R.lv + ii;
-            const double u = *pa, w = *pb;
-            *pa = cs * u - sn * w;
-            *pb = sn * u + cs * w;
-          }
-          rot = 1;
-        }
-        __syncthreads();
-        if (rnd + 1 < np - 1)
-          ok = rows_pair_dots(cc, R, Wl, xb + (size_t)((q + 1) & 1) * npairs * cc.P, rnd + 1, np, ncol, li);
-      }
-      const int any = __syncthreads_or(rot);
-      if (!any || cc.dead) break;
-    }
-  }
-  *sweeps_out = cc.dead ? maxsw : sweep;
+  const double tol64 = 16.0 * 2.220446049250313e-16 * sqrt((double)len);
+  const int sw = rows_sweeps<double>(cc, R, wa, Wl, Vl, ncol, li, vi, maxsw, tol64 * tol64, &s_nrot,
+                                      phase_acc);
+  *sweeps_out = sw;
+  *noconv = sw >= maxsw || cc.dead;
   if (exec_flops && threadIdx.x == 0) {
     // over the whole cluster: 6 per rotated element pair of W and V, 2 per
     // element of every pair's inner product, 2 per element of the norms
-    const double rounds = (double)imin(sweep + 1, maxsw) * (double)(np - 1);
-    *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * rounds * npairs * len +
-                  2.0 * (double)(imin(sweep + 1, maxsw) + 1) * ncol * len;
+    const int np = (ncol + 1) & ~1, npairs = np / 2;
+    const double sweeps = (double)imin(sw + 1, maxsw);
+    *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * sweeps * (np - 1) * npairs * len +
+                  2.0 * (sweeps + 1) * ncol * len;
   }
   // exact norms -> singular values, order and rank (identical in every CTA);
   // non-finite values order last and are reported
-  rows_norms(cc, R, wa, ncol, li);
+  rows_norms<double>(cc, R, wa, Wl, ncol, li);
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
     const double sv = sqrt(nrm[j]) / scl;
     if (!(sv >= 0.0) || isinf(sv)) { sig[j] = -1.0; atomicOr(cc.status, ST_NAN); }
@@ -585,8 +682,9 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
     pc.lap(PH_SVD_OUT);
     cl_command(cc, 2, ncol, len, maxsw, m, n, k, delta, scl);
     int sw = 0;
+    bool noconv = false;
     double xfl = 0.0;
-    const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw, &xfl);
+    const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw, &noconv, &xfl, pc.on ? pc.acc : nullptr);
     pc.lap(PH_JACOBI);
     if (threadIdx.x == 0) { pc.acc[PH_SVD64_FLOPS] += svd_flops(m, n); pc.acc[PH_SVD64_EXEC] += xfl; }
     const RowsLayout R = rows_layout(ncol, len, cc.P);
@@ -596,7 +694,7 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
     const double* tail = (const double*)(wa + R.tail);
     if (threadIdx.x == 0) {
       pc.acc[6] += sw; pc.acc[7] += 1.0;
-      if (sw >= maxsw) {
+      if (noconv) {
         flag(status, ST_NOCONV);
         if (atomicCAS(&status[1], 0, 1) == 0) {
           status[2] = blockIdx.x / cc.P; status[3] = k; status[4] = ncol; status[5] = len;
@@ -1246,7 +1344,8 @@ __device__ void round_worker(const RoundJob& J, int L_arg, ClusterCtx& cc) {
       jacobi64_cluster(cc, Wm, jacobi_ld<double>(len), Vm, jacobi_ld<double>(ncol), ncol, len, maxsw);
     } else if (op == 2) {
       int sw = 0;
-      svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw);
+      bool noconv = false;
+      svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw, &noconv);
     } else {
       break;
     }
@@ -1307,16 +1406,15 @@ void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T*
 
 template <typename T>
 int round_cluster_size(int njobs, int cap) {
-  // resident clusters of each size on this device (queried once per device)
+  // resident clusters of each size 1..16 on this device (queried once per device)
   static int cached_dev = -1;
-  static int max_active[5] = {0, 0, 0, 0, 0};      // sizes 1, 2, 4, 8, 16
+  static int max_active[CL_MAX + 1];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
   if (dev != cached_dev) {
     cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)round_smem_bytes());
     cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    for (int e = 0; e < 5; ++e) {
-      const int P = 1 << e;
+    for (int P = 1; P <= CL_MAX; ++P) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(P, 1, 1);
       cfg.blockDim = dim3(RT, 1, 1);
@@ -1330,15 +1428,15 @@ int round_cluster_size(int njobs, int cap) {
       cfg.numAttrs = 1;
       int n = 0;
       if (cudaOccupancyMaxActiveClusters(&n, round_kernel<T>, &cfg) != cudaSuccess) n = 0;
-      max_active[e] = n;
+      max_active[P] = n;
     }
     cudaGetLastError();
     cached_dev = dev;
   }
-  for (int e = 4; e >= 1; --e) {
-    const int P = 1 << e;
-    if (P <= cap && max_active[e] >= njobs) return P;
-  }
+  // the largest cluster at which every job of the launch is resident at once
+  // (the FP64 Jacobi scales with the SMs of its cluster)
+  for (int P = imin(cap, CL_MAX); P >= 2; --P)
+    if (max_active[P] >= njobs) return P;
   return 1;
 }
 

@@ -15,7 +15,8 @@ HADAMARD_FIT, HADAMARD_EXACT, HADAMARD_ZIPUP = 0, 1, 2
 TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy", "zipup")
 ROUND_PHASES = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus", "jacobi_sweeps", "svd_count",
-                "jacobi_global", "svd_global_count", "svd64_flops", "svd64_exec_flops")
+                "jacobi_global", "svd_global_count", "svd64_flops", "svd64_exec_flops", "rx_norms", "rx_dots",
+                "rx_wait", "rx_angle", "rx_rot")
 
 c_int_p = ctypes.POINTER(ctypes.c_int)
 c_double_p = ctypes.POINTER(ctypes.c_double)
@@ -69,6 +70,8 @@ class Stats(ctypes.Structure):
         ("product_jobs_per_step", ctypes.c_int),
         ("mass", ctypes.c_double),
         ("discarded2", ctypes.c_double),
+        ("round_ctas_per_step", ctypes.c_int),
+        ("max_cluster", ctypes.c_int),
     ]
 
 

@@ -129,7 +129,7 @@ def test_argument_errors_of_the_precision_and_failure_options(lib):
     c.chi_max = 8
     c.eps = 1e-8
     c.precision = nat.MIXED
-    for field, bad in (("max_cluster", 3), ("max_cluster", 32), ("max_cluster", -1),
+    for field, bad in (("max_cluster", 17), ("max_cluster", 32), ("max_cluster", -1),
                        ("jacobi_max_sweeps", -1), ("wait_limit_ns", -5)):
         setattr(c, field, bad)
         assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1, field
