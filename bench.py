@@ -564,7 +564,7 @@ def main():
     peaks = load_peaks()
     rd = prof["round"]
     per_launch_ms = rd["ms"] / max(rd["launches"], 1)
-    phase_keys = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus")
+    phase_keys = ("terms", "gemm_rw", "qr", "jacobi32", "jacobi", "svd_out", "gemm_qus")
     phase_tot = max(sum(ph[q] for q in phase_keys), 1.0)
     roofline = {"kernel": "round_kernel", "launches_per_step": rd["launches"],
                 "ms_per_launch": per_launch_ms,

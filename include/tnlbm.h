@@ -232,15 +232,19 @@ enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_
  * kernel class: device milliseconds ms[TNLBM_K_COUNT] (CUDA events after every
  * launch), algorithmic FLOPs flops[] (counted on the device from the realised
  * bonds: 2MNK per GEMM, LAPACK-style counts for QR and SVD), and launches[].
- * phases (nullable, 17 doubles): SM cycles of the rounding kernel's phases
+ * phases (nullable, 22 doubles): SM cycles of the rounding kernel's phases
  * summed over its jobs: term formation, R*W product, QR, Jacobi, SVD outputs,
  * Q*US product (indices 0..5); Jacobi sweeps and SVD count (6, 7); Jacobi
  * cycles and count of the SVDs whose matrices did not fit in shared memory
  * (8, 9); FLOPs of the FP64 centre SVDs of TNLBM_MIXED / cluster runs: the
  * algorithmic (Golub-Kahan) count 4 M N^2 + 8 N^3 (10) and the FP64 FLOPs
- * the cluster Jacobi executed (11); cycles of the cluster Jacobi (leader CTA)
- * in the column norms, forming and sending the pair inner products, waiting
- * for the other CTAs' parts, the rotation angles and the rotations (12..16). */
+ * the cluster Jacobi executed (11); cycles of the cluster Jacobi's FP64
+ * sweeps (leader CTA) in the column norms, forming and sending the pair inner
+ * products, waiting for the other CTAs' parts, the rotation angles and the
+ * rotations (12..16); for TNLBM_MIXED the cycles of the leader's FP32 sweeps,
+ * of the Newton-Schulz step and of the product X V that start the FP64
+ * sweeps, and the FP32 sweeps (17..20); rounds of the FP64 cluster sweeps
+ * (21). */
 int tnlbm_profile_step(tnlbm_sim *s, double *ms, double *flops, int *launches, double *phases);
 int tnlbm_destroy(tnlbm_sim *s); /* NULL-safe */
 const char *tnlbm_last_error(void);

@@ -35,13 +35,17 @@ enum : int { C_ROUND = 0, C_FIT_GEMM = 1, C_FIT_QR = 2, C_FIT_MISC = 3, C_RHO0 =
 // slots 6..9: Jacobi sweeps, SVD count, Jacobi cycles and count of SVDs in
 // global memory; 10: algorithmic FLOPs of the FP64 centre SVDs (Golub-Kahan
 // count); 11: FP64 FLOPs the cluster Jacobi executed (rotations, inner
-// products, norms); 12..16: cycles of the leader's cluster Jacobi spent in
-// the column norms (with their exchange), forming and sending the pair inner
-// products, waiting for the other CTAs' parts, the angles, and the rotations
+// products, norms); 12..16: cycles of the leader's FP64 cluster Jacobi
+// sweeps spent in the column norms (with their exchange), forming and sending
+// the pair inner products, waiting for the other CTAs' parts, the angles, and
+// the rotations; for FP32 data, 17: cycles of the leader's FP32 sweeps, 18: of
+// the Newton-Schulz step, 19: of the product X V, 20: the FP32 sweeps; 21:
+// rounds of the FP64 cluster sweeps
 enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT = 4, PH_GEMM_C = 5,
              PH_SVD64_FLOPS = 10, PH_SVD64_EXEC = 11, PH_RX_NORM = 12, PH_RX_DOT = 13, PH_RX_WAIT = 14,
-             PH_RX_ANGLE = 15, PH_RX_ROT = 16, PH_COUNT = 17 };
-static constexpr int CTR_SIZE = 24;   // >= C_COUNT + PH_COUNT
+             PH_RX_ANGLE = 15, PH_RX_ROT = 16, PH_J32 = 17, PH_NS = 18, PH_XV = 19, PH_SWEEPS32 = 20,
+             PH_ROUNDS64 = 21, PH_COUNT = 22 };
+static constexpr int CTR_SIZE = 32;   // >= C_COUNT + PH_COUNT
 // Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
 __host__ __device__ inline double qr_flops(double m, double n) {
   const double k = m < n ? m : n, big = m < n ? n : m;

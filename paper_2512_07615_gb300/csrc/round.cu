@@ -234,30 +234,35 @@ struct RxClock {
 
 // ---------------------------------------------------------------- row-partitioned FP64 SVD
 // Work-area layout (bytes, same in every CTA of the cluster) of svd64_rows:
-// the CTA's rows of W and V (doubles; the FP32 phase keeps its rows in the
-// first halves), the column norms, the exchange buffers of the pair inner
-// products and of the column norms, and the singular values / order / tails
-// the rank rule reads.
+// the CTA's rows of W (FP64; for FP32 data the rows of X and then of X V),
+// its rows of V (FP64), the column norms, each pair's rotation and flag, the
+// exchange buffers of the pair inner products and of the column norms, for
+// FP32 data the block of G = V0^T V0 and the staged rows of the Newton-Schulz
+// step, and the singular values, order and tails the rank rule reads.
 struct RowsLayout {
-  int lw, lv, npairs;
-  size_t wl, vl, nrm, pc, ps, pf, gl, xb, nbuf, sig, perm, tail, total;
+  int lw, lv, npairs, kc;
+  size_t wl, w2, vl, nrm, pcw, psw, pf, gl, xb, nbuf, gb, st, sig, perm, tail, total;
 };
-__host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
+__host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P, bool two_phase) {
   RowsLayout R;
   R.lw = (len + P - 1) / P;
   R.lv = (ncol + P - 1) / P;
   R.npairs = (ncol + 1) / 2;
+  R.kc = imax(1, imin(32, 2048 / imax(ncol, 1)));      // staged rows of V per chunk (<= 16 KB)
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~(size_t)15; return r; };
   R.wl = take((size_t)ncol * R.lw * 8);
+  R.w2 = two_phase ? take((size_t)ncol * R.lw * 8) : R.wl;
   R.vl = take((size_t)ncol * R.lv * 8);
   R.nrm = take((size_t)ncol * 8);
-  R.pc = take((size_t)R.npairs * 8);
-  R.ps = take((size_t)R.npairs * 8);
+  R.pcw = take((size_t)R.npairs * 8);
+  R.psw = take((size_t)R.npairs * 8);
   R.pf = take((size_t)R.npairs * 4);
   R.gl = take((size_t)imax(R.npairs, ncol) * 8);
   R.xb = take((size_t)2 * R.npairs * P * 8);
   R.nbuf = take((size_t)ncol * P * 8);
+  R.gb = two_phase ? take((size_t)ncol * R.lv * 8) : 0;
+  R.st = two_phase ? take((size_t)ncol * R.kc * 8) : 0;
   R.sig = take((size_t)ncol * 8);
   R.perm = take((size_t)ncol * 4);
   R.tail = take((size_t)(ncol + 2) * 8);
@@ -265,11 +270,17 @@ __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P) {
   return R;
 }
 
-// Sum of n doubles x[0], x[s], x[2s], ... in a fixed order with four
-// independent accumulators (a short dependency chain on the FP64 pipe); the
-// same inputs give the same double in every CTA.
-__device__ __forceinline__ double sum4(const double* x, int n, int s) {
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+template <typename S>
+__device__ __forceinline__ S fmx(S a, S b, S c) {
+  if constexpr (sizeof(S) == 8) return fma(a, b, c);
+  else return fmaf(a, b, c);
+}
+
+// Sum of n values x[0], x[s], x[2s], ... in a fixed order with four
+// independent accumulators; the same inputs give the same result in every CTA.
+template <typename S>
+__device__ __forceinline__ S sum4(const S* x, int n, int s) {
+  S a0 = 0, a1 = 0, a2 = 0, a3 = 0;
   int c = 0;
   for (; c + 3 < n; c += 4) {
     a0 += x[(size_t)c * s];
@@ -288,30 +299,29 @@ __device__ __forceinline__ void rr_pair(int rnd, int p, int np, int& a, int& b) 
   if (a > b) { const int t = a; a = b; b = t; }
 }
 
-// Column norms of W over the cluster: every CTA adds its rows (FP64 sums of
-// its S-typed entries), sends the partial sums to every CTA, and sums them in
-// rank order (the same order, so the same doubles, in every CTA).  Ends with
-// nrm[] valid everywhere.
+// Column norms of the S-typed rows Wl over the cluster, in S arithmetic:
+// every CTA sums its rows, sends the partial sums to every CTA, and every CTA
+// adds them in rank order (the same values in every CTA).  Ends with nrm[]
+// valid everywhere.
 template <typename S>
 __device__ inline void rows_norms(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, const S* Wl, int ncol,
                                   int li) {
-  // FP64 work goes one instruction per warp at a time whatever the active
-  // lanes, so every FP64 step here runs one thread per column, all lanes busy
-  double* nb = (double*)(wa + R.nbuf);
-  double* nrm = (double*)(wa + R.nrm);
-  double* loc = (double*)(wa + R.gl);
-  cl_xchg_expect(cc, (unsigned)(ncol * cc.P * 8));
+  S* nb = (S*)(wa + R.nbuf);
+  S* nrm = (S*)(wa + R.nrm);
+  S* loc = (S*)(wa + R.gl);
+  cl_xchg_expect(cc, (unsigned)(ncol * cc.P * sizeof(S)));
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
     const S* w = Wl + (size_t)j * R.lw;
-    double v0 = 0.0, v1 = 0.0;
+    S v0 = 0, v1 = 0, v2 = 0, v3 = 0;
     int ii = 0;
-    for (; ii + 1 < li; ii += 2) {
-      const double x0 = (double)w[ii], x1 = (double)w[ii + 1];
-      v0 += x0 * x0;
-      v1 += x1 * x1;
+    for (; ii + 3 < li; ii += 4) {
+      v0 = fmx(w[ii], w[ii], v0);
+      v1 = fmx(w[ii + 1], w[ii + 1], v1);
+      v2 = fmx(w[ii + 2], w[ii + 2], v2);
+      v3 = fmx(w[ii + 3], w[ii + 3], v3);
     }
-    if (ii < li) { const double x0 = (double)w[ii]; v0 += x0 * x0; }
-    const double v = v0 + v1;
+    for (; ii < li; ++ii) v0 = fmx(w[ii], w[ii], v0);
+    const S v = (v0 + v1) + (v2 + v3);
     if (cc.P == 1) nb[j] = v;
     else loc[j] = v;
   }
@@ -326,37 +336,43 @@ __device__ inline void rows_norms(ClusterCtx& cc, const RowsLayout& R, unsigned 
       }
   }
   cl_xchg_wait(cc);
-  for (int j = threadIdx.x; j < ncol; j += blockDim.x) nrm[j] = sum4(nb + (size_t)j * cc.P, cc.P, 1);
+  for (int j = threadIdx.x; j < ncol; j += blockDim.x) nrm[j] = sum4<S>(nb + (size_t)j * cc.P, cc.P, 1);
   __syncthreads();
 }
 
-// This CTA's parts of the inner products of every pair of round rnd (FP64
-// sums), sent to every CTA's exchange slots xq[p][rank]; then the cluster
-// barrier.
+// This CTA's parts of the inner products of the pairs of round rnd (S sums;
+// four lanes per pair, so that the FP64 work of a round is spread over four
+// warps), sent to every CTA's exchange slots xq[p][rank]; then the wait for
+// the other CTAs' parts.
 template <typename S>
 __device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, const S* Wl,
-                                      double* xq, int rnd, int np, int ncol, int li, RxClock& rx) {
+                                      S* xq, int rnd, int np, int ncol, int li, RxClock& rx) {
   const int npairs = np / 2;
-  double* loc = (double*)(wa + R.gl);
-  cl_xchg_expect(cc, (unsigned)(npairs * cc.P * 8));
-  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+  S* loc = (S*)(wa + R.gl);
+  cl_xchg_expect(cc, (unsigned)(npairs * cc.P * sizeof(S)));
+  for (int t = threadIdx.x; t < npairs * 4; t += blockDim.x) {
+    const int p = t >> 2, q = t & 3;
+    const unsigned grp = 0xfu << (threadIdx.x & 28);
     int a, b;
     rr_pair(rnd, p, np, a, b);
-    double g = 0.0;
+    S g0 = 0, g1 = 0;
     if (b < ncol) {
-      const S* wa_ = Wl + (size_t)a * R.lw;
-      const S* wb_ = Wl + (size_t)b * R.lw;
-      double g0 = 0.0, g1 = 0.0;
-      int ii = 0;
-      for (; ii + 1 < li; ii += 2) {
-        g0 += (double)wa_[ii] * (double)wb_[ii];
-        g1 += (double)wa_[ii + 1] * (double)wb_[ii + 1];
+      const S* x = Wl + (size_t)a * R.lw;
+      const S* y = Wl + (size_t)b * R.lw;
+      int ii = q;
+      for (; ii + 4 < li; ii += 8) {
+        g0 = fmx(x[ii], y[ii], g0);
+        g1 = fmx(x[ii + 4], y[ii + 4], g1);
       }
-      if (ii < li) g0 += (double)wa_[ii] * (double)wb_[ii];
-      g = g0 + g1;
+      if (ii < li) g0 = fmx(x[ii], y[ii], g0);
     }
-    if (cc.P == 1) xq[p] = g;
-    else loc[p] = g;
+    S g = g0 + g1;
+    g += __shfl_xor_sync(grp, g, 1, 4);
+    g += __shfl_xor_sync(grp, g, 2, 4);
+    if (q == 0) {
+      if (cc.P == 1) xq[p] = g;
+      else loc[p] = g;
+    }
   }
   if (cc.P > 1) {
     __syncthreads();
@@ -372,93 +388,147 @@ __device__ inline bool rows_pair_dots(ClusterCtx& cc, const RowsLayout& R, unsig
   return ok;
 }
 
-// Rotation of a pair with norms al, be and inner product g (all exchanged
-// FP64 values, identical in every CTA), for rows of type S: false if the pair
-// counts as orthogonal (g^2 <= tol2 al be) or a column is negligible.
-// t = tan(theta) is Rutishauser's root, evaluated in FP32 (for |zeta| > 1e18,
-// a column near zero against a large one, t = 1 / (2 zeta) in FP64, where the
-// FP32 quotient would overflow).  FP64 rows: c = (1 + t^2)^(-1/2) by two FP64
-// Newton steps from the FP32 value and s = c t, so the rotation is orthogonal
-// to FP64 accuracy and an angle off by FP32 round-off only leaves a residual
-// the next sweep removes.  FP32 rows: c, s in FP32.  The new norms are
-// al - t g and be + t g (exact for the exact root; recomputed every sweep).
+// (c, s) of FP32 values renormalised in FP64: (c, s) (1 + d)^(-1/2) with
+// d = c^2 + s^2 - 1 (exact in FP64: the squares have 48 bits) and the series
+// to d^2 (error O(d^3) ~ 1e-20): orthogonal to FP64 rounding.
+__device__ __forceinline__ void renorm64(float cf, float sf, double& c, double& s) {
+  const double c0 = (double)cf, s0 = (double)sf;
+  const double dr = fma(c0, c0, s0 * s0) - 1.0;
+  const double h = fma(dr, fma(0.375, dr, -0.5), 1.0);
+  c = c0 * h;
+  s = s0 * h;
+}
+
+// Rotation of a pair with norms al, be and inner product g (exchanged values,
+// identical in every CTA): false if the pair counts as orthogonal
+// (g^2 <= tol2 al be) or a column is negligible.  t = tan(theta) is
+// Rutishauser's root of the FP32 quotient zeta = (be - al) / (2 g) (for
+// S = double the difference is taken in FP64, and a quotient outside the
+// FP32 range is formed in FP64, with t = 1 / (2 zeta) once |zeta| > 1e18).
+// c = (1 + t^2)^(-1/2) and s = c t are FP32; for S = double (and for every
+// rotation of V, see renorm64) they are taken renormalised in FP64, so that
+// each rotation is orthogonal to FP64 rounding; for S = float W turns by the
+// FP32 (c, s).  The new norms are al - t g and be + t g (exact for the exact
+// root; recomputed every sweep).
 template <typename S>
-__device__ __forceinline__ bool rows_angle(double al, double be, double g, double tol2, S& cs, S& sn,
-                                           double& na, double& nb) {
-  const double amin = sizeof(S) == 8 ? 1e-250 : 1e-60;
-  if (g == 0.0 || !(al > amin) || !(be > amin) || g * g <= tol2 * al * be) return false;
-  const double zd = (be - al) / (2.0 * g);
-  double t;
-  if (fabs(zd) > 1e18) {
-    t = 0.5 / zd;
-  } else {
-    const float zeta = (float)zd;
-    const float az = fabsf(zeta);
-    t = (double)copysignf(1.f / (az + sqrtf(1.f + zeta * zeta)), zeta);
-  }
-  double c, s;
+__device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw, S& na, S& nb) {
+  S amin;
+  if constexpr (sizeof(S) == 8) amin = 1e-250;
+  else amin = 1e-30f;
+  if (g == (S)0 || !(al > amin) || !(be > amin) || g * g <= tol2 * al * be) return false;
+  const S d = be - al;
+  float tf;
+  S t;
+  bool tiny = false;
   if constexpr (sizeof(S) == 8) {
-    const double x = 1.0 + t * t;
-    c = (double)rsqrtf((float)x);
-    // two Newton steps from the FP32 estimate (relative error 2^-23 -> ~1e-14
-    // -> rounding): the rotation is orthogonal to FP64 rounding, so the
-    // thousands of rotations of one SVD do not drift the column scales
-    c = c * (1.5 - 0.5 * x * c * c);
-    c = c * (1.5 - 0.5 * x * c * c);
-    s = c * t;
+    if (fabs(d) > 1e18 * fabs(g) || fabs(g) < 1e-30) {
+      const double zd = d / (2.0 * g);                  // outside the FP32 range: FP64 (rare)
+      if (fabs(zd) > 1e18) {
+        t = 0.5 / zd;
+        tiny = true;
+      } else {
+        const float z = (float)zd;
+        tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
+        t = (double)tf;
+      }
+    } else {
+      const float z = (float)d / (2.f * (float)g);
+      tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
+      t = (double)tf;
+    }
   } else {
-    const float tf = (float)t;
-    if (tf == 0.f) return false;                      // below the FP32 range: nothing to rotate
-    const float cf = 1.f / sqrtf(1.f + tf * tf);
-    c = (double)cf;
-    s = (double)(cf * tf);
+    const float z = d / (2.f * g);
+    tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
+    if (tf == 0.f) return false;                        // below the FP32 range: nothing to rotate
+    t = tf;
   }
-  cs = (S)c;
-  sn = (S)s;
-  na = al - t * g;                                    // the rotated norms (recomputed every sweep)
+  if (tiny) {
+    cw = (S)1;                                          // 1 + t^2 rounds to 1 for |t| < 1e-18
+    sw = t;
+  } else {
+    const float cf = rsqrtf(fmaf(tf, tf, 1.f)), sf = cf * tf;
+    if constexpr (sizeof(S) == 8) {
+      renorm64(cf, sf, cw, sw);
+    } else {
+      cw = cf;
+      sw = sf;
+    }
+  }
+  na = al - t * g;
   nb = be + t * g;
   return true;
 }
 
-// Jacobi sweeps of the row-partitioned matrices (rows of type S) until a sweep
-// rotates nothing or maxsw sweeps; nrot counts rotations.  Returns the sweeps
-// used.
+// Cyclic one-sided Jacobi sweeps (round-robin order) on the cluster's rows of
+// W (type S: the arithmetic of the inner products, norms and angles) and of
+// V (FP64), until a sweep rotates nothing or maxsw sweeps; nrot counts
+// rotations, rounds the rounds.  Per round: each CTA's parts of the pair
+// inner products go to every CTA, four lanes per pair add them in rank order,
+// lane 0 takes the angle, and every CTA rotates its rows of W and V.
+// Returns the sweeps used.
 template <typename S>
-__device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, S* Wl, S* Vl, int ncol,
-                           int li, int vi, int maxsw, double tol2, unsigned* nrot, double* phase_acc) {
+__device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, S* Wl, double* Vl, int ncol,
+                           int li, int vi, int maxsw, S tol2, unsigned* nrot, double* phase_acc) {
   RxClock rx(phase_acc);
   unsigned q = 0;                                  // rounds so far (exchange buffer parity)
-  double* nrm = (double*)(wa + R.nrm);
-  double* xb = (double*)(wa + R.xb);
-  S* pcs = (S*)(wa + R.pc);
-  S* psn = (S*)(wa + R.ps);
+  S* nrm = (S*)(wa + R.nrm);
+  S* xb = (S*)(wa + R.xb);
+  S* pcw = (S*)(wa + R.pcw);
+  S* psw = (S*)(wa + R.psw);
   int* pfl = (int*)(wa + R.pf);
   const int np = (ncol + 1) & ~1, npairs = np / 2;
-  int sweep = 0;
+  int sweep = 0, rounds = 0;
   if (ncol < 2) return 0;
+  // rotation of this CTA's rows of V by round rnd's pairs (FP64, renormalised)
+  auto rotate_v = [&](int rnd) {
+    for (int idx = threadIdx.x; idx < npairs * vi; idx += blockDim.x) {
+      const int p = idx / vi, ii = idx - p * vi;
+      if (!pfl[p]) continue;
+      int a, b;
+      rr_pair(rnd, p, np, a, b);
+      double cs, sn;
+      if constexpr (sizeof(S) == 8) {
+        cs = pcw[p];
+        sn = psw[p];
+      } else {
+        renorm64(pcw[p], psw[p], cs, sn);
+      }
+      double* pa = Vl + (size_t)a * R.lv + ii;
+      double* pb = Vl + (size_t)b * R.lv + ii;
+      const double u = *pa, w = *pb;
+      *pa = cs * u - sn * w;
+      *pb = sn * u + cs * w;
+    }
+  };
   for (; sweep < maxsw; ++sweep) {
     rows_norms<S>(cc, R, wa, Wl, ncol, li);
     rx.lap(PH_RX_NORM);
     int any = 0;
     bool ok = rows_pair_dots<S>(cc, R, wa, Wl, xb + (size_t)(q & 1) * npairs * cc.P, 0, np, ncol, li, rx);
     for (int rnd = 0; rnd < np - 1 && ok; ++rnd, ++q) {
-      const double* xq = xb + (size_t)(q & 1) * npairs * cc.P;
-      // one thread per pair: gamma as the partials summed in rank order (the
-      // same doubles in every CTA), the angle and the new norms
+      const S* xq = xb + (size_t)(q & 1) * npairs * cc.P;
+      ++rounds;
       int rot = 0;
-      for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+      for (int t = threadIdx.x; t < npairs * 4; t += blockDim.x) {
+        const int p = t >> 2, l = t & 3;
+        const unsigned grp = 0xfu << (threadIdx.x & 28);
+        // the partials of pair p in rank order: lane l adds ranks l, l+4, ...,
+        // then the four lanes combine (the same order in every CTA)
+        S g = 0;
+        for (int c = l; c < cc.P; c += 4) g += xq[(size_t)p * cc.P + c];
+        g += __shfl_xor_sync(grp, g, 1, 4);
+        g += __shfl_xor_sync(grp, g, 2, 4);
+        if (l != 0) continue;
         int a, b;
         rr_pair(rnd, p, np, a, b);
         int go = 0;
         if (b < ncol) {
-          const double g = sum4(xq + (size_t)p * cc.P, cc.P, 1);
-          S cs, sn;
-          double na, nb;
-          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cs, sn, na, nb)) {
+          S cw, sw, na, nb;
+          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cw, sw, na, nb)) {
             nrm[a] = na;
             nrm[b] = nb;
-            pcs[p] = cs;
-            psn[p] = sn;
+            pcw[p] = cw;
+            psw[p] = sw;
             go = 1;
             atomicAdd(nrot, 1u);
           }
@@ -468,31 +538,20 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
       }
       any |= __syncthreads_or(rot);
       rx.lap(PH_RX_ANGLE);
-      // the rotations, one element pair per thread
+      // the rotations of W, one element pair per thread
       for (int idx = threadIdx.x; idx < npairs * li; idx += blockDim.x) {
-        const int p = idx / li, ii = idx % li;
+        const int p = idx / li, ii = idx - p * li;
         if (!pfl[p]) continue;
         int a, b;
         rr_pair(rnd, p, np, a, b);
-        const S cs = pcs[p], sn = psn[p];
+        const S cs = pcw[p], sn = psw[p];
         S* pa = Wl + (size_t)a * R.lw + ii;
         S* pb = Wl + (size_t)b * R.lw + ii;
         const S u = *pa, w = *pb;
         *pa = cs * u - sn * w;
         *pb = sn * u + cs * w;
       }
-      for (int idx = threadIdx.x; idx < npairs * vi; idx += blockDim.x) {
-        const int p = idx / vi, ii = idx % vi;
-        if (!pfl[p]) continue;
-        int a, b;
-        rr_pair(rnd, p, np, a, b);
-        const S cs = pcs[p], sn = psn[p];
-        S* pa = Vl + (size_t)a * R.lv + ii;
-        S* pb = Vl + (size_t)b * R.lv + ii;
-        const S u = *pa, w = *pb;
-        *pa = cs * u - sn * w;
-        *pb = sn * u + cs * w;
-      }
+      rotate_v(rnd);
       __syncthreads();
       rx.lap(PH_RX_ROT);
       if (rnd + 1 < np - 1)
@@ -501,29 +560,133 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
     }
     if (!any || cc.dead) break;
   }
+  if (phase_acc && threadIdx.x == 0) phase_acc[PH_ROUNDS64] += rounds;
   return cc.dead ? maxsw : sweep;
+}
+
+// Stage rows [k0, k0 + nk) of every column of the ncol x ncol matrix V
+// (global, column c at V + c * ld, type S) in shared memory as doubles:
+// st[c * kc + kk] = V(k0 + kk, c).
+template <typename S>
+__device__ inline void stage_rows(const S* V, int ld, int ncol, int k0, int nk, int kc, double* st) {
+  for (int idx = threadIdx.x; idx < ncol * nk; idx += blockDim.x) {
+    const int c = idx / nk, kk = idx - c * nk;
+    st[(size_t)c * kc + kk] = (double)__ldcg(V + (size_t)c * ld + k0 + kk);
+  }
+}
+
+// One Newton-Schulz step towards the orthogonal polar factor, in FP64, on
+// this CTA's block of columns J = [v0, v0 + vi): G(:, J) = V0^T V0(:, J),
+// V1(:, J) = V0 (3/2 I - 1/2 G)(:, J).  V0 (type S, ld0) and V1 (FP64, ld1)
+// are global; V0 is read in staged row chunks.  With V0^T V0 = I + E the
+// step leaves V1^T V1 = I + O(E^2) (3/4 E^2 to second order).
+template <typename S>
+__device__ inline void rows_ns_step(const RowsLayout& R, unsigned char* wa, const S* V0, int ld0, double* V1,
+                                    int ld1, int ncol, int v0, int vi) {
+  double* G = (double*)(wa + R.gb);                      // G[jj * ncol + i] = G(i, v0 + jj)
+  double* st = (double*)(wa + R.st);
+  const int kc = R.kc;
+  for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) G[idx] = 0.0;
+  for (int k0 = 0; k0 < ncol; k0 += kc) {
+    const int nk = imin(kc, ncol - k0);
+    __syncthreads();
+    stage_rows<S>(V0, ld0, ncol, k0, nk, kc, st);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
+      const int jj = idx / ncol, i = idx - jj * ncol;
+      const double* x = st + (size_t)i * kc;
+      const double* y = st + (size_t)(v0 + jj) * kc;
+      double a0 = 0.0, a1 = 0.0;
+      int kk = 0;
+      for (; kk + 1 < nk; kk += 2) {
+        a0 = fma(x[kk], y[kk], a0);
+        a1 = fma(x[kk + 1], y[kk + 1], a1);
+      }
+      if (kk < nk) a0 = fma(x[kk], y[kk], a0);
+      G[idx] += a0 + a1;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
+    const int jj = idx / ncol, i = idx - jj * ncol;
+    G[idx] = (i == v0 + jj ? 1.5 : 0.0) - 0.5 * G[idx];  // H = 3/2 I - 1/2 G
+  }
+  for (int k0 = 0; k0 < ncol; k0 += kc) {
+    const int nk = imin(kc, ncol - k0);
+    __syncthreads();
+    stage_rows<S>(V0, ld0, ncol, k0, nk, kc, st);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nk * vi; idx += blockDim.x) {
+      const int jj = idx / nk, kk = idx - jj * nk;
+      const double* h = G + (size_t)jj * ncol;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int i = 0;
+      for (; i + 3 < ncol; i += 4) {
+        a0 = fma(st[(size_t)i * kc + kk], h[i], a0);
+        a1 = fma(st[(size_t)(i + 1) * kc + kk], h[i + 1], a1);
+        a2 = fma(st[(size_t)(i + 2) * kc + kk], h[i + 2], a2);
+        a3 = fma(st[(size_t)(i + 3) * kc + kk], h[i + 3], a3);
+      }
+      for (; i < ncol; ++i) a0 = fma(st[(size_t)i * kc + kk], h[i], a0);
+      __stcg(V1 + (size_t)(v0 + jj) * ld1 + k0 + kk, (a0 + a1) + (a2 + a3));
+    }
+  }
+  __syncthreads();
+}
+
+// W2 = X V for this CTA's rows (FP64), V (ncol x ncol, global FP64, column
+// c at V + c * ld) read in staged row chunks; X and W2 in the rows layout.
+__device__ inline void rows_xv(const RowsLayout& R, unsigned char* wa, const double* X, const double* V, int ld,
+                               double* W2, int ncol, int li) {
+  double* st = (double*)(wa + R.st);
+  const int kc = R.kc;
+  for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) W2[(size_t)(idx / li) * R.lw + idx % li] = 0.0;
+  for (int k0 = 0; k0 < ncol; k0 += kc) {
+    const int nk = imin(kc, ncol - k0);
+    __syncthreads();
+    stage_rows<double>(V, ld, ncol, k0, nk, kc, st);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
+      const int j = idx / li, ii = idx - j * li;
+      const double* v = st + (size_t)j * kc;
+      double a0 = 0.0, a1 = 0.0;
+      int kk = 0;
+      for (; kk + 1 < nk; kk += 2) {
+        a0 = fma(X[(size_t)(k0 + kk) * R.lw + ii], v[kk], a0);
+        a1 = fma(X[(size_t)(k0 + kk + 1) * R.lw + ii], v[kk + 1], a1);
+      }
+      if (kk < nk) a0 = fma(X[(size_t)(k0 + kk) * R.lw + ii], v[kk], a0);
+      W2[(size_t)j * R.lw + ii] += a0 + a1;
+    }
+  }
+  __syncthreads();
 }
 
 // FP64 one-sided Jacobi SVD of the centre matrix C (m x n, T, global) with the
 // rows of the Jacobi matrices split over the CTAs of the cluster and held in
-// shared memory.  W = the columns of C (n <= m) or of C^T, scaled by scl; V
-// accumulates the rotations.  CTA c owns entries [c len / P, (c+1) len / P)
-// of every column of W and [c ncol / P, (c+1) ncol / P) of every column of V.
-// Per round of the round-robin tournament each CTA forms its parts of the
-// pair inner products gamma, all CTAs exchange them through distributed
-// shared memory and sum them in rank order, so every CTA takes the same
-// rotations and applies them to its rows; the stopping rule is the
-// single-CTA Jacobi's (16 eps_64 sqrt(len)).  Column norms are recomputed
-// exactly at the start of every sweep and at the end.  Every CTA then finds the
-// same singular values, order and kept rank (the rank rule of Eq. svd-move
-// with delta) and writes its rows of core k (V^T[:r], r x n) and of U S
-// (m x r).  Called by all threads of every CTA with equal arguments; returns
-// the kept rank (0 if it exceeds the bond capacity), the sweeps, whether the
-// sweep limit was reached, and the FP64 FLOPs executed.
+// shared memory.  X = the columns of C (n <= m) or of C^T, scaled by scl;
+// V accumulates the rotations (FP64).  CTA c owns entries
+// [c len / P, (c+1) len / P) of every column of W and [c ncol / P,
+// (c+1) ncol / P) of every column of V.  Every CTA sums the exchanged parts
+// in the same order, so every CTA takes the same rotations.
+// FP32 data (T = float): the leader has already run FP32 sweeps on X alone
+// and left their V0 (FP32, ncol x ncol) in the job's scratch; one FP64
+// Newton-Schulz step, spread over the CTAs by blocks of columns, makes it
+// orthogonal to FP64 working accuracy (V0^T V0 - I ~ 1e-6 becomes ~1e-12),
+// W = X V is formed in FP64 and the FP64 sweeps start from there -- the
+// result is an FP64 one-sided Jacobi SVD of X started from the FP32 sweeps'
+// V.  FP64 data start from W = X, V = I.  Column norms are recomputed
+// exactly at the start of every sweep and at the end.  Every CTA then finds
+// the same singular values, order and kept rank (the rank rule of Eq.
+// svd-move with delta) and writes its rows of core k (V^T[:r], r x n) and of
+// U S (m x r).  Called by all threads of every CTA with equal arguments;
+// returns the kept rank (0 if it exceeds the bond capacity), the FP64
+// sweeps, whether their limit was reached, and the FP64 FLOPs executed.
 template <typename T>
 __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m, int n, double scl, double delta,
                           int maxsw, int* sweeps_out, bool* noconv, double* exec_flops = nullptr,
                           double* phase_acc = nullptr) {
+  constexpr bool two_phase = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_nrot;
   if (threadIdx.x == 0) s_nrot = 0;
@@ -534,7 +697,7 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
   T* out = (T*)J.dst.base + core_offset(L, J.dst.cap, k);
   const int ncol = imin(m, n), len = imax(m, n);
   const bool trans = (n <= m);
-  const RowsLayout R = rows_layout(ncol, len, cc.P);
+  const RowsLayout R = rows_layout(ncol, len, cc.P, two_phase);
   double* Wl = (double*)(wa + R.wl);
   double* Vl = (double*)(wa + R.vl);
   double* nrm = (double*)(wa + R.nrm);
@@ -543,33 +706,53 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
   double* tail = (double*)(wa + R.tail);
   const int i0 = cc.rank * len / cc.P, li = (cc.rank + 1) * len / cc.P - i0;
   const int v0 = cc.rank * ncol / cc.P, vi = (cc.rank + 1) * ncol / cc.P - v0;
-  // own rows of W (promoted, scaled) and of V = I
+  // own rows of X (promoted, scaled by a power of two: exact)
   for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
     const int j = idx / li, ii = idx % li, i = i0 + ii;
     const T v = trans ? __ldcg(C + (size_t)i * n + j) : __ldcg(C + (size_t)j * n + i);
     Wl[(size_t)j * R.lw + ii] = scl * (double)v;
   }
-  for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
-    const int j = idx / vi, ii = idx % vi;
-    Vl[(size_t)j * R.lv + ii] = (j == v0 + ii) ? 1.0 : 0.0;
+  double* W = Wl;
+  if constexpr (two_phase) {
+    const long long t0 = clock64();
+    const float* V0 = (const float*)(scr + J.lay.jv_off);
+    const int ld0 = jacobi_ld<float>(ncol), ld1 = jacobi_ld<double>(ncol);
+    double* V1 = (double*)(scr + J.lay.jv64_off);
+    rows_ns_step<float>(R, wa, V0, ld0, V1, ld1, ncol, v0, vi);
+    cl_sync(cc);                                  // every block of V1 written (cluster-scope fence)
+    if (phase_acc && threadIdx.x == 0) phase_acc[PH_NS] += (double)(clock64() - t0);
+    const long long t1 = clock64();
+    for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
+      const int j = idx / vi, ii = idx % vi;
+      Vl[(size_t)j * R.lv + ii] = __ldcg(V1 + (size_t)j * ld1 + v0 + ii);
+    }
+    W = (double*)(wa + R.w2);
+    rows_xv(R, wa, Wl, V1, ld1, W, ncol, li);
+    if (phase_acc && threadIdx.x == 0) phase_acc[PH_XV] += (double)(clock64() - t1);
+  } else {
+    for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
+      const int j = idx / vi, ii = idx % vi;
+      Vl[(size_t)j * R.lv + ii] = (j == v0 + ii) ? 1.0 : 0.0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const double tol64 = 16.0 * 2.220446049250313e-16 * sqrt((double)len);
-  const int sw = rows_sweeps<double>(cc, R, wa, Wl, Vl, ncol, li, vi, maxsw, tol64 * tol64, &s_nrot,
-                                      phase_acc);
+  const int sw = rows_sweeps<double>(cc, R, wa, W, Vl, ncol, li, vi, maxsw, tol64 * tol64, &s_nrot, phase_acc);
   *sweeps_out = sw;
   *noconv = sw >= maxsw || cc.dead;
   if (exec_flops && threadIdx.x == 0) {
-    // over the whole cluster: 6 per rotated element pair of W and V, 2 per
-    // element of every pair's inner product, 2 per element of the norms
+    // over the whole cluster, FP64 only: 6 per rotated element pair of W and
+    // V, 2 per element of every pair's inner product and of the norms; for
+    // FP32 data the Newton-Schulz step (two ncol^3 products) and X V
     const int np = (ncol + 1) & ~1, npairs = np / 2;
     const double sweeps = (double)imin(sw + 1, maxsw);
     *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * sweeps * (np - 1) * npairs * len +
                   2.0 * (sweeps + 1) * ncol * len;
+    if (two_phase) *exec_flops += 4.0 * (double)ncol * ncol * ncol + 2.0 * (double)len * ncol * ncol;
   }
   // exact norms -> singular values, order and rank (identical in every CTA);
   // non-finite values order last and are reported
-  rows_norms<double>(cc, R, wa, Wl, ncol, li);
+  rows_norms<double>(cc, R, wa, W, ncol, li);
   for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
     const double sv = sqrt(nrm[j]) / scl;
     if (!(sv >= 0.0) || isinf(sv)) { sig[j] = -1.0; atomicOr(cc.status, ST_NAN); }
@@ -610,14 +793,14 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
       }
       for (int idx = threadIdx.x; idx < li * r; idx += blockDim.x) {
         const int ii = idx / r, jr = idx % r;
-        __stcg(US + (size_t)(i0 + ii) * r + jr, (T)(Wl[(size_t)perm[jr] * R.lw + ii] * (1.0 / scl)));
+        __stcg(US + (size_t)(i0 + ii) * r + jr, (T)(W[(size_t)perm[jr] * R.lw + ii] * (1.0 / scl)));
       }
     } else {
       for (int idx = threadIdx.x; idx < r * li; idx += blockDim.x) {
         const int jr = idx / li, ii = idx % li;
         const int pj = perm[jr];
         const double sg = sig[pj] * scl;
-        const double v = sg > 0.0 ? Wl[(size_t)pj * R.lw + ii] / sg : (i0 + ii == jr ? 1.0 : 0.0);
+        const double v = sg > 0.0 ? W[(size_t)pj * R.lw + ii] / sg : (i0 + ii == jr ? 1.0 : 0.0);
         __stcg(out + (size_t)jr * n + i0 + ii, (T)v);
       }
       for (int idx = threadIdx.x; idx < vi * r; idx += blockDim.x) {
@@ -677,9 +860,30 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
   __syncthreads();
   const double scl = sh.tau[1];
   const int maxsw = J.max_sweeps > 0 ? J.max_sweeps : 60;
-  if (!in_smem && cc.P > 1 && rows_layout(ncol, len, cc.P).total <= (size_t)SM_WORK) {
+  if (!in_smem && cc.P > 1 && rows_layout(ncol, len, cc.P, sizeof(T) == 4).total <= (size_t)SM_WORK) {
     // rows of the Jacobi matrices spread over the cluster, in shared memory
     pc.lap(PH_SVD_OUT);
+    if constexpr (sizeof(T) == 4) {
+      // FP32 data: FP32 sweeps on X by this CTA alone (the in-CTA Jacobi of the
+      // FP32 path; its own stopping rule, at most 30 sweeps, convergence not
+      // required), V0 left in the job's scratch for the cluster
+      const int ldw32 = jacobi_ld<float>(len), ldv32 = jacobi_ld<float>(ncol);
+      const size_t need32 = ((size_t)ncol * ldw32 + (size_t)ncol * ldv32) * sizeof(float);
+      float* Vg = (float*)(scr + J.lay.jv_off);
+      float* Wf = need32 <= (size_t)SM_WORK ? (float*)work : (float*)(scr + J.lay.jw_off);
+      float* Vf = need32 <= (size_t)SM_WORK ? (float*)work + (size_t)ncol * ldw32 : Vg;
+      for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
+        const int jj = idx / len, i = idx % len;
+        Wf[(size_t)jj * ldw32 + i] = (float)(scl * (double)(trans ? C[(size_t)i * n + jj] : C[(size_t)jj * n + i]));
+      }
+      __syncthreads();
+      const int sw32 = jacobi_cols_fast<float>(Wf, ldw32, Vf, ldv32, ncol, len, imin(maxsw, 30));
+      if (Vf != Vg)
+        for (int idx = threadIdx.x; idx < ncol * ldv32; idx += blockDim.x) __stcg(Vg + idx, Vf[idx]);
+      __syncthreads();
+      if (threadIdx.x == 0) pc.acc[PH_SWEEPS32] += sw32;
+      pc.lap(PH_J32);
+    }
     cl_command(cc, 2, ncol, len, maxsw, m, n, k, delta, scl);
     int sw = 0;
     bool noconv = false;
@@ -687,7 +891,7 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
     const int r = svd64_rows<T>(cc, J, L, k, m, n, scl, delta, maxsw, &sw, &noconv, &xfl, pc.on ? pc.acc : nullptr);
     pc.lap(PH_JACOBI);
     if (threadIdx.x == 0) { pc.acc[PH_SVD64_FLOPS] += svd_flops(m, n); pc.acc[PH_SVD64_EXEC] += xfl; }
-    const RowsLayout R = rows_layout(ncol, len, cc.P);
+    const RowsLayout R = rows_layout(ncol, len, cc.P, sizeof(T) == 4);
     const unsigned char* wa = (const unsigned char*)work;
     const double* sig = (const double*)(wa + R.sig);
     const int* perm = (const int*)(wa + R.perm);

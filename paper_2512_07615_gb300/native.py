@@ -16,7 +16,7 @@ TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
 KERNEL_CLASSES = ("round", "fit_gemm", "fit_qr", "fit_misc", "rho0", "copy", "zipup")
 ROUND_PHASES = ("terms", "gemm_rw", "qr", "jacobi", "svd_out", "gemm_qus", "jacobi_sweeps", "svd_count",
                 "jacobi_global", "svd_global_count", "svd64_flops", "svd64_exec_flops", "rx_norms", "rx_dots",
-                "rx_wait", "rx_angle", "rx_rot")
+                "rx_wait", "rx_angle", "rx_rot", "jacobi32", "newton_schulz", "xv", "sweeps32", "rounds64")
 
 c_int_p = ctypes.POINTER(ctypes.c_int)
 c_double_p = ctypes.POINTER(ctypes.c_double)
