@@ -234,14 +234,15 @@ struct RxClock {
 
 // ---------------------------------------------------------------- row-partitioned FP64 SVD
 // Work-area layout (bytes, same in every CTA of the cluster) of svd64_rows:
-// the CTA's rows of W (FP64; for FP32 data the rows of X and then of X V),
-// its rows of V (FP64), the column norms, each pair's rotation and flag, the
-// exchange buffers of the pair inner products and of the column norms, for
-// FP32 data the block of G = V0^T V0 and the staged rows of the Newton-Schulz
-// step, and the singular values, order and tails the rank rule reads.
+// the CTA's rows of W and of V (FP64), the column norms, each pair's rotation
+// and flag, the exchange buffers of the pair inner products and of the
+// column norms, and the singular values, order and tails the rank rule
+// reads.  For FP32 data the block of G = V0^T V0 and the staged rows of V and
+// of X used by the Newton-Schulz step and by W = X V share the exchange
+// buffers' space (those run before the first exchange of the sweeps).
 struct RowsLayout {
   int lw, lv, npairs, kc;
-  size_t wl, w2, vl, nrm, pcw, psw, pf, gl, xb, nbuf, gb, st, sig, perm, tail, total;
+  size_t wl, vl, nrm, pcw, psw, pf, gl, xb, nbuf, gb, st, xs, sig, perm, tail, total;
 };
 __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P, bool two_phase) {
   RowsLayout R;
@@ -251,18 +252,25 @@ __host__ __device__ inline RowsLayout rows_layout(int ncol, int len, int P, bool
   R.kc = imax(1, imin(32, 2048 / imax(ncol, 1)));      // staged rows of V per chunk (<= 16 KB)
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 15) & ~(size_t)15; return r; };
+  auto rnd16 = [](size_t bytes) { return (bytes + 15) & ~(size_t)15; };
   R.wl = take((size_t)ncol * R.lw * 8);
-  R.w2 = two_phase ? take((size_t)ncol * R.lw * 8) : R.wl;
   R.vl = take((size_t)ncol * R.lv * 8);
   R.nrm = take((size_t)ncol * 8);
   R.pcw = take((size_t)R.npairs * 8);
   R.psw = take((size_t)R.npairs * 8);
   R.pf = take((size_t)R.npairs * 4);
   R.gl = take((size_t)imax(R.npairs, ncol) * 8);
-  R.xb = take((size_t)2 * R.npairs * P * 8);
-  R.nbuf = take((size_t)ncol * P * 8);
-  R.gb = two_phase ? take((size_t)ncol * R.lv * 8) : 0;
-  R.st = two_phase ? take((size_t)ncol * R.kc * 8) : 0;
+  // shared region: exchange buffers | Newton-Schulz and X V staging
+  const size_t xch = rnd16((size_t)2 * R.npairs * P * 8) + rnd16((size_t)ncol * P * 8);
+  const size_t stg = two_phase ? rnd16((size_t)ncol * R.lv * 8) + rnd16((size_t)ncol * R.kc * 8) +
+                                     rnd16((size_t)R.lw * R.kc * 8)
+                               : 0;
+  const size_t base = take(xch > stg ? xch : stg);
+  R.xb = base;
+  R.nbuf = base + rnd16((size_t)2 * R.npairs * P * 8);
+  R.gb = base;
+  R.st = base + rnd16((size_t)ncol * R.lv * 8);
+  R.xs = R.st + rnd16((size_t)ncol * R.kc * 8);
   R.sig = take((size_t)ncol * 8);
   R.perm = take((size_t)ncol * 4);
   R.tail = take((size_t)(ncol + 2) * 8);
@@ -634,17 +642,25 @@ __device__ inline void rows_ns_step(const RowsLayout& R, unsigned char* wa, cons
   __syncthreads();
 }
 
-// W2 = X V for this CTA's rows (FP64), V (ncol x ncol, global FP64, column
-// c at V + c * ld) read in staged row chunks; X and W2 in the rows layout.
-__device__ inline void rows_xv(const RowsLayout& R, unsigned char* wa, const double* X, const double* V, int ld,
-                               double* W2, int ncol, int li) {
+// W = X V for this CTA's rows (FP64): X(i, k) = scl C(i, k) (C^T when the
+// Jacobi runs on the columns of C^T) for the rows [i0, i0 + li), read from
+// the job's scratch, and V (ncol x ncol, FP64, column c at V + c * ld), both
+// staged in chunks of kc indices k.
+template <typename T>
+__device__ inline void rows_xv(const RowsLayout& R, unsigned char* wa, const T* C, int n, bool trans, double scl,
+                               int i0, int li, const double* V, int ld, double* W, int ncol) {
   double* st = (double*)(wa + R.st);
+  double* xs = (double*)(wa + R.xs);                      // xs[kk * li + ii] = X(i0 + ii, k0 + kk)
   const int kc = R.kc;
-  for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) W2[(size_t)(idx / li) * R.lw + idx % li] = 0.0;
+  for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) W[(size_t)(idx / li) * R.lw + idx % li] = 0.0;
   for (int k0 = 0; k0 < ncol; k0 += kc) {
     const int nk = imin(kc, ncol - k0);
     __syncthreads();
     stage_rows<double>(V, ld, ncol, k0, nk, kc, st);
+    for (int idx = threadIdx.x; idx < nk * li; idx += blockDim.x) {
+      const int kk = idx / li, ii = idx - kk * li, i = i0 + ii, k = k0 + kk;
+      xs[idx] = scl * (double)__ldcg(trans ? C + (size_t)i * n + k : C + (size_t)k * n + i);
+    }
     __syncthreads();
     for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
       const int j = idx / li, ii = idx - j * li;
@@ -652,11 +668,11 @@ __device__ inline void rows_xv(const RowsLayout& R, unsigned char* wa, const dou
       double a0 = 0.0, a1 = 0.0;
       int kk = 0;
       for (; kk + 1 < nk; kk += 2) {
-        a0 = fma(X[(size_t)(k0 + kk) * R.lw + ii], v[kk], a0);
-        a1 = fma(X[(size_t)(k0 + kk + 1) * R.lw + ii], v[kk + 1], a1);
+        a0 = fma(xs[kk * li + ii], v[kk], a0);
+        a1 = fma(xs[(kk + 1) * li + ii], v[kk + 1], a1);
       }
-      if (kk < nk) a0 = fma(X[(size_t)(k0 + kk) * R.lw + ii], v[kk], a0);
-      W2[(size_t)j * R.lw + ii] += a0 + a1;
+      if (kk < nk) a0 = fma(xs[kk * li + ii], v[kk], a0);
+      W[(size_t)j * R.lw + ii] += a0 + a1;
     }
   }
   __syncthreads();
@@ -706,12 +722,6 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
   double* tail = (double*)(wa + R.tail);
   const int i0 = cc.rank * len / cc.P, li = (cc.rank + 1) * len / cc.P - i0;
   const int v0 = cc.rank * ncol / cc.P, vi = (cc.rank + 1) * ncol / cc.P - v0;
-  // own rows of X (promoted, scaled by a power of two: exact)
-  for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
-    const int j = idx / li, ii = idx % li, i = i0 + ii;
-    const T v = trans ? __ldcg(C + (size_t)i * n + j) : __ldcg(C + (size_t)j * n + i);
-    Wl[(size_t)j * R.lw + ii] = scl * (double)v;
-  }
   double* W = Wl;
   if constexpr (two_phase) {
     const long long t0 = clock64();
@@ -726,10 +736,16 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
       const int j = idx / vi, ii = idx % vi;
       Vl[(size_t)j * R.lv + ii] = __ldcg(V1 + (size_t)j * ld1 + v0 + ii);
     }
-    W = (double*)(wa + R.w2);
-    rows_xv(R, wa, Wl, V1, ld1, W, ncol, li);
+    rows_xv<T>(R, wa, C, n, trans, scl, i0, li, V1, ld1, W, ncol);
+    cl_sync(cc);                                  // the staging space is the exchange buffers' again
     if (phase_acc && threadIdx.x == 0) phase_acc[PH_XV] += (double)(clock64() - t1);
   } else {
+    // own rows of X (promoted, scaled by a power of two: exact)
+    for (int idx = threadIdx.x; idx < ncol * li; idx += blockDim.x) {
+      const int j = idx / li, ii = idx % li, i = i0 + ii;
+      const T v = trans ? __ldcg(C + (size_t)i * n + j) : __ldcg(C + (size_t)j * n + i);
+      Wl[(size_t)j * R.lw + ii] = scl * (double)v;
+    }
     for (int idx = threadIdx.x; idx < ncol * vi; idx += blockDim.x) {
       const int j = idx / vi, ii = idx % vi;
       Vl[(size_t)j * R.lv + ii] = (j == v0 + ii) ? 1.0 : 0.0;

