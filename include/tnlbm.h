@@ -61,10 +61,14 @@ enum {
  *   TNLBM_MIXED  FP32 cores, contractions and QR sweeps; the centre SVD of every
  *                rounding step (Eq. svd-move: the singular values whose tail is
  *                the discarded weight, and the kept singular vectors) by an
- *                FP64 one-sided Jacobi on the FP32 centre matrix, with the
- *                Gram sums, norms and tails in FP64.  On one GPU the Jacobi of
- *                a rounding is shared by a thread-block cluster of up to 16
- *                CTAs (tnlbm_config.max_cluster). */
+ *                FP64 one-sided Jacobi on the FP32 centre matrix X, run to the
+ *                FP64 stopping rule, with the inner products, norms and tails
+ *                in FP64.  It starts from the V of FP32 sweeps on X, made
+ *                orthogonal in FP64 by one Newton-Schulz step (W = X V formed
+ *                in FP64).  On one GPU the FP64 part of a rounding is shared by
+ *                a thread-block cluster of up to 16 CTAs
+ *                (tnlbm_config.max_cluster); with one CTA per job the FP64
+ *                Jacobi runs from V = I. */
 enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2, TNLBM_MIXED = 3 };
 enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
 enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1, TNLBM_HADAMARD_ZIPUP = 2 };
