@@ -762,13 +762,46 @@ __device__ double qr_zero_floor2(const T* A, int m, int n, int lda, T* red) {
   }
 }
 
+// Sum over the block in the norm type N (double, or float for the scaled FP32
+// norms); `red` is shared scratch of >= 32 doubles.
+template <typename N>
+__device__ inline N block_sum_n(N v, double* red) {
+  if constexpr (sizeof(N) == 8) {
+    return block_sum(v, red);
+  } else {
+    N* r = (N*)red;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) r[wid] = v;
+    __syncthreads();
+    N s = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    if (wid == 0) {
+      s = lane < nw ? r[lane] : (N)0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) r[0] = s;
+    }
+    __syncthreads();
+    s = r[0];
+    __syncthreads();
+    return s;
+  }
+}
+
+// Householder QR, blocked by panels of QB columns.  Column norms and the
+// reflector scalars: FP64 for FP64 data; for FP32 data FP32 on the matrix
+// scaled by 2^-e (2^e the power of two at max|A|, an exact scaling), so that no
+// square of an entry above the zero floor (2^-60 max|A|) leaves the FP32
+// normal range.
 template <typename T>
 __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T* R, int ldr,
                                    double* tau, T* wv, double* red, T* vb, T* wb) {
+  using N = T;                                     // type of the norms and reflector scalars
   const int kk = imin(m, n);
   const int G = 8;                                 // threads per column in the panel dots
   __shared__ T s_scale;
-  __shared__ double s_norm2;
+  __shared__ N s_norm2;
   __shared__ T sT[QB][QB + 1], sG[QB][QB + 1];
   __shared__ signed char s_dneg[1024];
   T* redT = (T*)red;
@@ -776,31 +809,50 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
   T* W = wb + (size_t)QNG * QB * n;
   // columns below the zero floor: a reflector built from them would not be
   // orthogonal and would spoil the larger columns it is applied to
-  const double floor2 = qr_zero_floor2<T>(A, m, n, lda, redT);
+  N floor2, sc2;                                   // floor of the scaled squared norms; the scaling
+  if constexpr (sizeof(T) == 8) {
+    floor2 = qr_zero_floor2<T>(A, m, n, lda, redT);
+    sc2 = 1.0;
+  } else {
+    T amax = (T)0;
+    for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x)
+      amax = fmaxf(amax, fabsf(A[(size_t)(idx / n) * lda + idx % n]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) redT[threadIdx.x >> 5] = amax;
+    __syncthreads();
+    T mx = (T)0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) mx = fmaxf(mx, redT[w]);
+    __syncthreads();
+    int e = 0;
+    if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);
+    sc2 = ldexpf(1.f, -e);                         // max |A| sc2 in [0.5, 1)
+    floor2 = (float)m * 7.523164e-37f;             // m (2^-60)^2 in scaled units
+  }
   for (int p0 = 0; p0 < kk; p0 += QB) {
     const int pe = imin(p0 + QB, kk), pb = pe - p0;
-    {                                              // norm of column p0 below its diagonal (FP64 sum)
-      double part = 0.0;
+    {                                              // norm of column p0 below its diagonal
+      N part = 0;
       for (int i = p0 + 1 + threadIdx.x; i < m; i += blockDim.x) {
-        const double v = (double)A[(size_t)i * lda + p0];
+        const N v = (N)A[(size_t)i * lda + p0] * sc2;
         part += v * v;
       }
-      const double t = block_sum(part, red);
+      const N t = block_sum_n<N>(part, red);
       if (threadIdx.x == 0) s_norm2 = t;
     }
     // ---- panel: column by column, updates restricted to the panel
     for (int j = p0; j < pe; ++j) {
       if (threadIdx.x == 0) {
-        const double sig2 = s_norm2;
-        const double alpha = (double)A[(size_t)j * lda + j];
+        const N sig2 = s_norm2;
+        const N alpha = (N)A[(size_t)j * lda + j] * sc2;
         if (sig2 <= floor2) {
           tau[j] = 0.0;
-          s_scale = sig2 == 0.0 ? (T)0 : (T)-1;    // -1: zero the column below the diagonal
+          s_scale = sig2 == (N)0 ? (T)0 : (T)-1;   // -1: zero the column below the diagonal
         } else {
-          const double beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
-          tau[j] = (beta - alpha) / beta;
-          s_scale = (T)(1.0 / (alpha - beta));
-          A[(size_t)j * lda + j] = (T)beta;
+          const N beta = -copysign(sqrt(alpha * alpha + sig2), alpha);
+          tau[j] = (double)((beta - alpha) / beta);
+          s_scale = (T)(sc2 / (alpha - beta));
+          A[(size_t)j * lda + j] = (T)(beta / sc2);
         }
       }
       __syncthreads();
@@ -823,7 +875,7 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
         }
         __syncthreads();
       }
-      double part = 0.0;
+      N part = 0;
       if (tj != (T)0) {
         const int rows = m - j;
         if (nc > 0) {
@@ -832,19 +884,22 @@ __device__ void householder_qr_blk(T* A, int m, int n, int lda, T* Q, int ldq, T
             const T vi = (ii == j) ? (T)1 : sc * A[(size_t)ii * lda + j];
             const T nv = A[(size_t)ii * lda + c] - wv[c] * vi;
             A[(size_t)ii * lda + c] = nv;
-            if (c == j + 1 && ii > j + 1) part += (double)nv * (double)nv;
+            if (c == j + 1 && ii > j + 1) {
+              const N v = (N)nv * sc2;
+              part += v * v;
+            }
           }
         }
         __syncthreads();
         for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[(size_t)i * lda + j] *= sc;
       } else if (nc > 0) {
         for (int i = j + 2 + threadIdx.x; i < m; i += blockDim.x) {
-          const double v = (double)A[(size_t)i * lda + j + 1];
+          const N v = (N)A[(size_t)i * lda + j + 1] * sc2;
           part += v * v;
         }
       }
       if (j + 1 < pe) {
-        const double t = block_sum(part, red);
+        const N t = block_sum_n<N>(part, red);
         if (threadIdx.x == 0) s_norm2 = t;
       } else {
         __syncthreads();

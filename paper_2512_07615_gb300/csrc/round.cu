@@ -453,6 +453,13 @@ __device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw
   if (tiny) {
     cw = (S)1;                                          // 1 + t^2 rounds to 1 for |t| < 1e-18
     sw = t;
+  } else if (sizeof(S) == 8 && fabsf(tf) < 6.1035156e-05f) {
+    // |t| < 2^-14 (most rotations of the FP64 sweeps): c = 1 - t^2/2 and
+    // s = t c give c^2 + s^2 = 1 - 3 t^4 / 4 + ..., orthogonal to FP64 rounding
+    const double td = (double)tf;
+    const double c = fma(-0.5 * td, td, 1.0);
+    cw = (S)c;
+    sw = (S)(td * c);
   } else {
     const float cf = rsqrtf(fmaf(tf, tf, 1.f)), sf = cf * tf;
     if constexpr (sizeof(S) == 8) {
