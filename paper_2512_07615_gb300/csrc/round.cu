@@ -419,11 +419,13 @@ __device__ __forceinline__ void renorm64(float cf, float sf, double& c, double& 
 // FP32 (c, s).  The new norms are al - t g and be + t g (exact for the exact
 // root; recomputed every sweep).
 template <typename S>
-__device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw, S& na, S& nb) {
+__device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw, S& na, S& nb, float& rel2) {
   S amin;
   if constexpr (sizeof(S) == 8) amin = 1e-250;
   else amin = 1e-30f;
-  if (g == (S)0 || !(al > amin) || !(be > amin) || g * g <= tol2 * al * be) return false;
+  const S gg = g * g, ab = al * be;
+  if (g == (S)0 || !(al > amin) || !(be > amin) || gg <= tol2 * ab) return false;
+  rel2 = (float)gg / (float)ab;                         // g^2 / (al be); +inf if al be leaves the FP32 range
   const S d = be - al;
   float tf;
   S t;
@@ -476,14 +478,22 @@ __device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw
 
 // Cyclic one-sided Jacobi sweeps (round-robin order) on the cluster's rows of
 // W (type S: the arithmetic of the inner products, norms and angles) and of
-// V (FP64), until a sweep rotates nothing or maxsw sweeps; nrot counts
-// rotations, rounds the rounds.  Per round: each CTA's parts of the pair
+// V (FP64); nrot counts rotations.  Per round: each CTA's parts of the pair
 // inner products go to every CTA, four lanes per pair add them in rank order,
 // lane 0 takes the angle, and every CTA rotates its rows of W and V.
-// Returns the sweeps used.
+// Stopping rule: a sweep that rotates nothing (every pair within the
+// tolerance), or, for FP64 rows, a sweep whose largest relative inner
+// product g^2 / (al be) was below (5e-9)^2 -- Jacobi converges quadratically,
+// so its rotations leave every pair below ~(5e-9)^2 ncol plus the FP32 angle's
+// residual 1.2e-7 x 5e-9, under the tolerance 16 eps_64 sqrt(len) >= 5e-15,
+// and the confirming sweep is skipped.  Every CTA sees the same values, so
+// every CTA stops at the same sweep.  Returns the sweeps used; *converged
+// tells whether the rule was met within maxsw sweeps.
 template <typename S>
 __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, S* Wl, double* Vl, int ncol,
-                           int li, int vi, int maxsw, S tol2, unsigned* nrot, double* phase_acc) {
+                           int li, int vi, int maxsw, S tol2, unsigned* nrot, double* phase_acc, bool* converged,
+                           int* rounds_out = nullptr) {
+  __shared__ float s_mrel[32];
   RxClock rx(phase_acc);
   unsigned q = 0;                                  // rounds so far (exchange buffer parity)
   S* nrm = (S*)(wa + R.nrm);
@@ -493,7 +503,9 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
   int* pfl = (int*)(wa + R.pf);
   const int np = (ncol + 1) & ~1, npairs = np / 2;
   int sweep = 0, rounds = 0;
+  *converged = true;
   if (ncol < 2) return 0;
+  *converged = false;
   // rotation of this CTA's rows of V by round rnd's pairs (FP64, renormalised)
   auto rotate_v = [&](int rnd) {
     for (int idx = threadIdx.x; idx < npairs * vi; idx += blockDim.x) {
@@ -519,6 +531,7 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
     rows_norms<S>(cc, R, wa, Wl, ncol, li);
     rx.lap(PH_RX_NORM);
     int any = 0;
+    float mrel = 0.f;                              // largest g^2 / (al be) this thread rotated this sweep
     bool ok = rows_pair_dots<S>(cc, R, wa, Wl, xb + (size_t)(q & 1) * npairs * cc.P, 0, np, ncol, li, rx);
     for (int rnd = 0; rnd < np - 1 && ok; ++rnd, ++q) {
       const S* xq = xb + (size_t)(q & 1) * npairs * cc.P;
@@ -539,7 +552,9 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
         int go = 0;
         if (b < ncol) {
           S cw, sw, na, nb;
-          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cw, sw, na, nb)) {
+          float rel2 = 0.f;
+          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cw, sw, na, nb, rel2)) {
+            mrel = fmaxf(mrel, rel2);
             nrm[a] = na;
             nrm[b] = nb;
             pcw[p] = cw;
@@ -573,10 +588,23 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
         ok = rows_pair_dots<S>(cc, R, wa, Wl, xb + (size_t)((q + 1) & 1) * npairs * cc.P, rnd + 1, np, ncol, li,
                                rx);
     }
-    if (!any || cc.dead) break;
+    if (cc.dead) break;
+    if (!any) { *converged = true; break; }
+    if constexpr (sizeof(S) == 8) {
+      // the sweep's largest relative inner product (the same in every CTA)
+      for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
+      if ((threadIdx.x & 31) == 0) s_mrel[threadIdx.x >> 5] = mrel;
+      __syncthreads();
+      float m = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_mrel[w]);
+      __syncthreads();
+      if (m < 2.5e-17f) { *converged = true; ++sweep; break; }
+    }
   }
   if (phase_acc && threadIdx.x == 0) phase_acc[PH_ROUNDS64] += rounds;
-  return cc.dead ? maxsw : sweep;
+  if (rounds_out) *rounds_out = rounds;
+  if (cc.dead) { *converged = false; return maxsw; }
+  return sweep;
 }
 
 // Stage rows [k0, k0 + nk) of every column of the ncol x ncol matrix V
@@ -760,16 +788,19 @@ __device__ int svd64_rows(ClusterCtx& cc, const RoundJob& J, int L, int k, int m
     __syncthreads();
   }
   const double tol64 = 16.0 * 2.220446049250313e-16 * sqrt((double)len);
-  const int sw = rows_sweeps<double>(cc, R, wa, W, Vl, ncol, li, vi, maxsw, tol64 * tol64, &s_nrot, phase_acc);
+  bool conv = false;
+  int rounds = 0;
+  const int sw = rows_sweeps<double>(cc, R, wa, W, Vl, ncol, li, vi, maxsw, tol64 * tol64, &s_nrot, phase_acc,
+                                     &conv, &rounds);
   *sweeps_out = sw;
-  *noconv = sw >= maxsw || cc.dead;
+  *noconv = !conv || cc.dead;
   if (exec_flops && threadIdx.x == 0) {
     // over the whole cluster, FP64 only: 6 per rotated element pair of W and
     // V, 2 per element of every pair's inner product and of the norms; for
     // FP32 data the Newton-Schulz step (two ncol^3 products) and X V
     const int np = (ncol + 1) & ~1, npairs = np / 2;
-    const double sweeps = (double)imin(sw + 1, maxsw);
-    *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * sweeps * (np - 1) * npairs * len +
+    const double sweeps = (double)rounds / (double)imax(np - 1, 1);
+    *exec_flops = 6.0 * (double)s_nrot * (len + ncol) + 2.0 * (double)rounds * npairs * len +
                   2.0 * (sweeps + 1) * ncol * len;
     if (two_phase) *exec_flops += 4.0 * (double)ncol * ncol * ncol + 2.0 * (double)len * ncol * ncol;
   }
