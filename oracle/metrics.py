@@ -7,7 +7,8 @@ compression_ratio NVPS_ref / NVPS with NVPS_ref = (2^n)^D
 nvps_binary       NVPS of an MPS with binary sites from its realised bonds
 
 Pinned by tests/test_oracle_metrics.py against the compression ratios printed
-in Sec. 4 (TGV, aneurysm, pin-fin) and App. A.
+in Sec. 4 (TGV, aneurysm, pin-fin) and App. A; nvps_binary against the number
+of values held by TT-SVD cores and by the product state.
 """
 
 import numpy as np

@@ -19,3 +19,19 @@ def test_full_rank_mps_has_no_compression():
 def test_rel_l2():
     assert metrics.rel_l2([3.0, 4.0], [3.0, 4.0]) == 0.0
     assert abs(metrics.rel_l2([0.0, 0.0], [3.0, 4.0]) - 1.0) < 1e-15
+
+
+def test_nvps_binary_counts_the_stored_values():
+    """NVPS of a binary-site MPS is the number of values its cores hold: pinned
+    by the product state (2 L values), by the two-site full-rank MPS (bonds
+    1, 2, 1: 8 values) and by the sizes of TT-SVD cores of a random tensor
+    (ragged bonds 2, 4, ..., 4, 2)."""
+    import numpy as np
+    from oracle import mps as M
+    L = 7
+    assert metrics.nvps_binary([1] * (L + 1)) == 2 * L
+    assert metrics.nvps_binary([1, 2, 1]) == 8
+    x = np.random.default_rng(3).standard_normal((2,) * L)
+    cores = M.tt_svd(x, 64, 0.0)
+    assert M.ranks(cores) == [1, 2, 4, 8, 8, 4, 2, 1]
+    assert metrics.nvps_binary(M.ranks(cores)) == sum(c.size for c in cores)
