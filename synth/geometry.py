@@ -73,7 +73,6 @@ def vessel_tree(n_bits, root_radius, depth, seed, length_factor=3.0,
     N = 1 << n_bits
     rng = np.random.default_rng(seed)
     c = np.arange(N, dtype=np.float64) + 0.5
-    grid = np.stack(np.meshgrid(c, c, c, indexing="ij"), axis=-1)
     fluid = np.zeros((N, N, N), dtype=bool)
     start = np.array([0.25 * N, 0.5 * N, 0.5 * N])
     stack = [(start, np.array([1.0, 0.0, 0.0]), float(root_radius), 0)]
@@ -81,7 +80,12 @@ def vessel_tree(n_bits, root_radius, depth, seed, length_factor=3.0,
         p0, direction, r, gen = stack.pop()
         seg_len = length_factor * r
         p1 = p0 + seg_len * direction
-        fluid |= _segment_mask(N, p0, p1, r, grid)
+        # only the cells of the segment's bounding box can lie within r of it
+        lo = np.maximum(np.floor(np.minimum(p0, p1) - r - 1.0).astype(int), 0)
+        hi = np.minimum(np.ceil(np.maximum(p0, p1) + r + 1.0).astype(int), N)
+        if np.all(hi > lo):
+            sub = np.stack(np.meshgrid(c[lo[0]:hi[0]], c[lo[1]:hi[1]], c[lo[2]:hi[2]], indexing="ij"), axis=-1)
+            fluid[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] |= _segment_mask(N, p0, p1, r, sub)
         if gen + 1 >= depth:
             continue
         # an orthonormal frame around the parent axis
