@@ -924,7 +924,10 @@ __device__ __noinline__ int svd64_site(const RoundJob& J, int L, int k, const T*
       const int ldw32 = jacobi_ld<float>(len), ldv32 = jacobi_ld<float>(ncol);
       const size_t need32 = ((size_t)ncol * ldw32 + (size_t)ncol * ldv32) * sizeof(float);
       float* Vg = (float*)(scr + J.lay.jv_off);
-      float* Wf = need32 <= (size_t)SM_WORK ? (float*)work : (float*)(scr + J.lay.jw_off);
+      // W (the hot operand: len entries per rotated column) in shared memory
+      // whenever it fits there alone; V with it if both fit, else in scratch
+      const bool w_smem = (size_t)ncol * ldw32 * sizeof(float) <= (size_t)SM_WORK;
+      float* Wf = w_smem ? (float*)work : (float*)(scr + J.lay.jw_off);
       float* Vf = need32 <= (size_t)SM_WORK ? (float*)work + (size_t)ncol * ldw32 : Vg;
       for (int idx = threadIdx.x; idx < ncol * len; idx += blockDim.x) {
         const int jj = idx / len, i = idx % len;
@@ -1404,10 +1407,12 @@ __device__ void round_job_body(const RoundJob& J, int L_arg, int n_bits_arg, con
     if (!done && !full64) {
       if (ncol > MAXK) { if (threadIdx.x == 0) flag(status, ST_CAPACITY); return; }
       const bool trans = (n <= m);             // Jacobi on the columns of C
-      // 16-byte row strides (vector loads in the Jacobi); shared memory if it fits
+      // 16-byte row strides (vector loads in the Jacobi); shared memory if it
+      // fits -- W alone when W and V do not fit together
       const int ldw = jacobi_ld<T>(len), ldv = jacobi_ld<T>(ncol);
       const size_t need = ((size_t)ncol * ldw + (size_t)ncol * ldv) * sizeof(T);
-      T* Wm = (need <= (size_t)SM_WORK) ? work : scr + J.lay.jw_off;
+      const bool w_smem = (size_t)ncol * ldw * sizeof(T) <= (size_t)SM_WORK;
+      T* Wm = w_smem ? work : scr + J.lay.jw_off;
       T* Vm = (need <= (size_t)SM_WORK) ? work + (size_t)ncol * ldw : scr + J.lay.jv_off;
       const int ldw_e = ldw;
       const int ldv_e = ldv;
