@@ -258,3 +258,28 @@ def test_mixed_tgv_64cubed_tau_0_5076_tracks_dense_energy(tl):
     assert dev <= 1e-3
     assert sim.stats()["status"] == 0
     sim.close()
+
+
+@pytest.mark.parametrize("prec,gate", [(0, 1e-12), (3, 5e-6)])
+def test_rounding_at_chi_256_on_a_full_cluster(tl, prec, gate):
+    """The rounding at chi 256 (the branching-vessel configuration's bond):
+    the sum of two random MPS of L = 18 sites with bonds up to 128 each gives
+    centre matrices of 256 x 512, whose FP64 Jacobi fills the shared memory of
+    a 16-CTA cluster (row layout of 172 KB per CTA).  Untruncated (chi 256
+    holds every summed bond, eps 0), so the result is the exact sum: FP64
+    within 1e-12 of the oracle, the mixed mode within FP32 storage."""
+    from paper_2512_07615_gb300 import tnlbm as T
+    nat = tl.native
+    L, cap = 18, 256
+    A = synth.random_mps(L, synth.feasible_ranks(L, 128), 71)
+    B = synth.random_mps(L, synth.feasible_ranks(L, 128), 72)
+    if prec == 3:
+        A, B = ([c.astype(np.float32).astype(np.float64) for c in X] for X in (A, B))
+    dA, dB = (T.DeviceMps.from_cores(X, cap, prec) for X in (A, B))
+    dst = T.DeviceMps(L, cap, prec)
+    T.lincomb_round([[T.plain(dA, 1.0), T.plain(dB, -0.75)]], [dst], cap, 0.0)
+    ref = M.lincomb_round([(1.0, A), (-0.75, B)], cap, 0.0)
+    assert max(dst.bonds()) == 256
+    err = rel(M.to_tensor(dst.cores()), M.to_tensor(ref))
+    print("chi 256 rounding prec %d: rel-L2 = %.3e" % (prec, err))
+    assert err <= gate
