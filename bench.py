@@ -45,7 +45,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "mixed": 3}
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "mixed": 3, "bf16": 4}
 PREC_NAME = {v: k for k, v in PREC.items()}
 
 WORKLOADS = {
@@ -404,13 +404,16 @@ def cpu_threads():
 
 # ------------------------------------------------------------------ main
 def precision_desc(p):
+    svd64 = ("fp64 one-sided Jacobi (cluster of CTAs, started from fp32 sweeps made orthogonal by an fp64 "
+             "Newton-Schulz step), fp64 norms and tails")
     return {0: dict(storage="fp64", contractions="fp64 SIMT", qr="fp64", svd="fp64 one-sided Jacobi"),
-            1: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (fp64 column norms)",
+            1: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (scaled fp32 column norms)",
                     svd="fp32 one-sided Jacobi, fp64 tails"),
             2: dict(storage="fp32", contractions="tf32 tensor cores (fit), fp32 SIMT (rounding)",
-                    qr="fp32 (fp64 column norms)", svd="fp32 one-sided Jacobi, fp64 tails"),
-            3: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (fp64 column norms)",
-                    svd="fp64 one-sided Jacobi (cluster of CTAs), fp64 norms and tails")}[p]
+                    qr="fp32 (scaled fp32 column norms)", svd="fp32 one-sided Jacobi, fp64 tails"),
+            3: dict(storage="fp32", contractions="fp32 SIMT", qr="fp32 (scaled fp32 column norms)", svd=svd64),
+            4: dict(storage="fp32", contractions="bf16 x bf16 -> fp32 tensor cores (fit), fp32 SIMT (rounding)",
+                    qr="fp32 (scaled fp32 column norms)", svd=svd64)}[p]
 
 
 def reference_arm(args, w, solid, modes, config, N3, rank):
@@ -578,7 +581,7 @@ def main():
                 "traffic": None,
                 "traffic_note": "the rounding kernel reads its terms and writes its result once per job; "
                                 "DRAM bytes per launch are in profiles/ (ncu), not re-measured per run"}
-    if w["precision"] in (0, 3):
+    if w["precision"] in (0, 3, 4):
         # the centre SVDs are FP64 one-sided Jacobis bound by the FP64 pipes:
         # achieved = the kernel's algorithmic FLOPs (QR, SVD by the Golub-Kahan
         # count, GEMMs) per launch / launch time, against the FP64 GEMM peak
@@ -598,12 +601,17 @@ def main():
         roofline.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                          "frac": ach / peak if peak else None,
                          "peak_source": "FP32 (no TF32) torch.matmul on this pool (profiles/peaks_gb300.md)"})
-    if w["precision"] == 2 and prof["fit_gemm"]["ms"] > 0:
-        tf32_peak = peaks.get("tf32_tflops")
+    if w["precision"] in (2, 4) and prof["fit_gemm"]["ms"] > 0:
+        # the fit's contractions on the tensor cores: TF32 against the measured
+        # TF32 GEMM peak, BF16 against the driver's measured BF16 burst peak
+        if w["precision"] == 2:
+            tc_peak, src = peaks.get("tf32_tflops"), "TF32 torch.matmul on this pool (profiles/peaks_gb300.md)"
+        else:
+            tc_peak, src = peaks.get("bf16_tflops"), "BF16 torch.matmul burst on this pool (MEASURED_PEAKS.json)"
         ach_tc = prof["fit_gemm"]["flops"] / (prof["fit_gemm"]["ms"] / 1e3) / 1e12
-        roofline["tensor"] = {"kernel": "fit_gemm_tc", "bound": "tensor", "achieved": ach_tc, "peak": tf32_peak,
-                              "unit": "TFLOP/s", "frac": ach_tc / tf32_peak if tf32_peak else None,
-                              "peak_source": "TF32 torch.matmul on this pool (profiles/peaks_gb300.md)"}
+        roofline["tensor"] = {"kernel": "fit_gemm_tc", "bound": "tensor", "achieved": ach_tc, "peak": tc_peak,
+                              "unit": "TFLOP/s", "frac": ach_tc / tc_peak if tc_peak else None,
+                              "peak_source": src}
 
     # end to end through the C ABI: populations host -> device, step, device -> host
     e2e = None
@@ -653,7 +661,7 @@ def main():
                                               "sensitivity: chi-capped bonds and variational products)",
                "fp64_baseline": ({"value": cmp["fp64_value"], "unit": "MLUPS", "ms_per_step": cmp["fp64_ms_per_step"]}
                                  if cmp else None),
-               "dtype": {0: "f64", 1: "f32", 2: "tf32", 3: "f32+f64svd"}[w["precision"]],
+               "dtype": {0: "f64", 1: "f32", 2: "tf32", 3: "f32+f64svd", 4: "bf16+f32+f64svd"}[w["precision"]],
                "data": "synthetic", "config": config,
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},

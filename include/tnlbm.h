@@ -24,8 +24,8 @@
  *     tnlbm_mps_offset(L, cap, k); inside the slot the core is packed
  *     [r_k][2][r_(k+1)] row-major with its realised bonds r.  Realised bonds
  *     are an int32 array r[0..L] with r[0] = r[L] = 1.
- *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32, TNLBM_TF32 and
- *     TNLBM_MIXED buffers float.
+ *   - precision: TNLBM_FP64 buffers hold double, TNLBM_FP32, TNLBM_TF32,
+ *     TNLBM_MIXED and TNLBM_BF16 buffers float.
  *   - stream arguments are cudaStream_t values passed as void* (NULL = legacy
  *     default stream).  Primitive calls are asynchronous on that stream unless
  *     stated; they allocate their own scratch with cudaMalloc and free it
@@ -68,8 +68,11 @@ enum {
  *                in FP64).  On one GPU the FP64 part of a rounding is shared by
  *                a thread-block cluster of up to 16 CTAs
  *                (tnlbm_config.max_cluster); with one CTA per job the FP64
- *                Jacobi runs from V = I. */
-enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2, TNLBM_MIXED = 3 };
+ *                Jacobi runs from V = I.
+ *   TNLBM_BF16   as TNLBM_MIXED, with the fit's core contractions on the tensor
+ *                cores as BF16 x BF16 products summed in FP32 (tcgen05.mma
+ *                kind::f16); cores and every other contraction stay FP32. */
+enum { TNLBM_FP64 = 0, TNLBM_FP32 = 1, TNLBM_TF32 = 2, TNLBM_MIXED = 3, TNLBM_BF16 = 4 };
 enum { TNLBM_D3Q19 = 19, TNLBM_D3Q15 = 15 };
 enum { TNLBM_HADAMARD_FIT = 0, TNLBM_HADAMARD_EXACT = 1, TNLBM_HADAMARD_ZIPUP = 2 };
 
@@ -96,12 +99,12 @@ typedef struct {
   int chi_max;             /* bond cap chi of every rounding (Sec. 2.1)        */
   double eps;              /* relative rounding tolerance: keep the smallest
                               rank whose discarded tail is <= eps*||T||/sqrt(L-1) */
-  int precision;           /* TNLBM_FP64, TNLBM_FP32, TNLBM_TF32 or TNLBM_MIXED
-                              (see the enum above).  Near tau = 1/2 (weakly
+  int precision;           /* TNLBM_FP64, TNLBM_FP32, TNLBM_TF32, TNLBM_MIXED or
+                              TNLBM_BF16 (see the enum above).  Near tau = 1/2 (weakly
                               damped flows) the FP32 one-sided Jacobi of
                               TNLBM_FP32 / TNLBM_TF32 leaves errors the
-                              collision does not damp: use TNLBM_MIXED or
-                              TNLBM_FP64                                       */
+                              collision does not damp: use TNLBM_MIXED,
+                              TNLBM_BF16 or TNLBM_FP64                          */
   int hadamard;            /* TNLBM_HADAMARD_FIT (Sec. 2.3, default), _EXACT
                               (Eq. mul followed by a rounding) or _ZIPUP (the
                               zip-up pass, then a rounding; chi_max <= 512)     */
@@ -287,7 +290,8 @@ typedef struct {
 /* dst[b] = round(sum_t terms[b*nterms + t]) : block-diagonal sum (Eq. add) of
  * the (exactly formed) terms, then a left-orthogonalising QR sweep and a
  * right-to-left truncated SVD sweep (Eq. svd-move) with bond cap chi_max and
- * relative tolerance eps.  dst capacity must be >= chi_max. */
+ * relative tolerance eps.  dst capacity must be >= chi_max.  TNLBM_BF16 rounds
+ * as TNLBM_MIXED (a rounding has no contraction that BF16 would take). */
 int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms,
                         const tnlbm_term *terms, void *const *dst,
                         int *const *dst_ranks, int dst_cap, int chi_max,
@@ -334,8 +338,9 @@ int tnlbm_hadamard_zipup(int precision, int n_bits, int batch,
 
 /* A[b] ~ B[b] . C[b] by the single-site variational fit of Sec. 2.3: candidate
  * A = B (bonds unchanged), `sweeps` round trips of local updates and QR/LQ
- * centre shifts.  A must have capacity >= B's.  precision TNLBM_TF32: float
- * buffers, the contractions on the tensor cores (TF32 operands). */
+ * centre shifts.  A must have capacity >= B's.  precision TNLBM_TF32 /
+ * TNLBM_BF16: float buffers, the contractions on the tensor cores (TF32 or
+ * BF16 operands, FP32 sums); TNLBM_MIXED: float buffers, FP32 contractions. */
 int tnlbm_hadamard_fit(int precision, int n_bits, int batch,
                        const void *const *B, const int *const *rB, int capB,
                        const void *const *C, const int *const *rC, int capC,

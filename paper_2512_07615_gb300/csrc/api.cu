@@ -446,16 +446,16 @@ struct Builder {
 
 // Options every rounding job of a simulation carries.
 static void set_round_options(const tnlbm_sim* s, RoundJob& rj) {
-  rj.svd64 = s->prec == TNLBM_MIXED ? 1 : 0;
+  rj.svd64 = prec_svd64(s->prec) ? 1 : 0;
   rj.max_sweeps = s->cfg.jacobi_max_sweeps;
   rj.wait_ns = s->cfg.wait_limit_ns;
 }
 
 // CTAs per rounding job for a launch of njobs jobs of a simulation: clusters
-// share the FP64 centre SVDs (TNLBM_MIXED and TNLBM_FP64); FP32 jobs run alone.
+// share the FP64 centre SVDs (TNLBM_MIXED, TNLBM_BF16 and TNLBM_FP64); FP32 jobs run alone.
 template <typename T>
 static int sim_cluster(const tnlbm_sim* s, int njobs) {
-  if (s->prec != TNLBM_MIXED && s->prec != TNLBM_FP64) return 1;
+  if (!prec_svd64(s->prec) && s->prec != TNLBM_FP64) return 1;
   const int cap = s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16;
   return cap <= 1 ? 1 : round_cluster_size<T>(njobs, cap);
 }
@@ -576,7 +576,7 @@ static int enqueue_step(tnlbm_sim* s, int* launches, Prof* prof = nullptr) {
     }
     if (!lv.fj.empty())
       n += run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, both ? s->s1 : s->s0, prof,
-                      s->prec == TNLBM_TF32);
+                      prec_tc(s->prec));
     if (!lv.zj.empty()) {
       n += run_zipup<T>(lv.d_zj, (int)lv.zj.size(), s->L, s->d_status, both ? s->s1 : s->s0, ctr);
       if (prof) prof->mark(C_ZIPUP);
@@ -936,7 +936,7 @@ int tnlbm_create(const tnlbm_config* cfg, tnlbm_sim** out) {
   if (C.chi_max < 1 || C.chi_max > 512) { set_error("chi_max must be in [1, 512]"); return TNLBM_E_ARG; }
   if (C.eps < 0.0) { set_error("eps must be >= 0"); return TNLBM_E_ARG; }
   if (C.precision != TNLBM_FP64 && C.precision != TNLBM_FP32 && C.precision != TNLBM_TF32 &&
-      C.precision != TNLBM_MIXED) {
+      C.precision != TNLBM_MIXED && C.precision != TNLBM_BF16) {
     set_error("bad precision");
     return TNLBM_E_ARG;
   }
@@ -1430,7 +1430,7 @@ static int lincomb_impl(int n_bits, int batch, int nterms, const tnlbm_term* ter
 }
 
 template <typename T>
-static int fit_impl(int n_bits, int batch, bool tc, const void* const* B, const int* const* rB, int capB,
+static int fit_impl(int n_bits, int batch, int tc, const void* const* B, const int* const* rB, int capB,
                     const void* const* C, const int* const* rC, int capC, void* const* A,
                     int* const* rA, int capA, int sweeps, cudaStream_t st) {
   const int L = 3 * n_bits;
@@ -1534,7 +1534,7 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const 
                         void* stream) {
   if (n_bits < 1 || n_bits > 10 || batch < 0 || nterms < 1 || nterms > TN_MAXT || !terms || !dst ||
       !dst_ranks || chi_max < 1 || chi_max > dst_cap || chi_max > 512 || eps < 0 || precision < TNLBM_FP64 ||
-      precision > TNLBM_MIXED) {
+      precision > TNLBM_BF16) {
     set_error("bad arguments to tnlbm_lincomb_round");
     return TNLBM_E_ARG;
   }
@@ -1543,7 +1543,7 @@ int tnlbm_lincomb_round(int precision, int n_bits, int batch, int nterms, const 
   return precision == TNLBM_FP64
              ? tn::lincomb_impl<double>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st)
              : tn::lincomb_impl<float>(n_bits, batch, nterms, terms, dst, dst_ranks, dst_cap, chi_max, eps, 0, st,
-                                       nullptr, precision == TNLBM_MIXED ? 1 : 0);
+                                       nullptr, prec_svd64(precision) ? 1 : 0);
 }
 
 int tnlbm_lincomb_round_rsvd(int precision, int n_bits, int batch, int nterms, const tnlbm_term* terms,
@@ -1610,7 +1610,7 @@ int tnlbm_hadamard_fit(int precision, int n_bits, int batch, const void* const* 
   cudaStream_t st = (cudaStream_t)stream;
   return precision == TNLBM_FP64
              ? tn::fit_impl<double>(n_bits, batch, false, B, rB, capB, C, rC, capC, A, rA, capA, sweeps, st)
-             : tn::fit_impl<float>(n_bits, batch, precision == TNLBM_TF32, B, rB, capB, C, rC, capC, A, rA, capA,
+             : tn::fit_impl<float>(n_bits, batch, prec_tc(precision), B, rB, capB, C, rC, capC, A, rA, capA,
                                    sweeps, st);
 }
 
@@ -1797,7 +1797,7 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
         auto& g = lv.fg[gi];
         if (!g.fj.empty())
           nl += run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->sfit[gi], nullptr,
-                           b->prec == TNLBM_TF32);
+                           prec_tc(b->prec));
         if (!g.zj.empty())
           nl += run_zipup<T>(g.d_zj, (int)g.zj.size(), b->lens[gi], b->d_status, b->sfit[gi], nullptr);
       }
@@ -1880,7 +1880,7 @@ static int batch_build(tnlbm_batch* b) {
       TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
       int cap = 16;
       for (tnlbm_sim* s : b->sims) cap = std::min(cap, s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16);
-      lv.cluster = (b->prec == TNLBM_MIXED || b->prec == TNLBM_FP64) && cap > 1
+      lv.cluster = (prec_svd64(b->prec) || b->prec == TNLBM_FP64) && cap > 1
                        ? round_cluster_size<T>((int)lv.rj.size(), cap) : 1;
     }
     for (auto& g : lv.fg) {

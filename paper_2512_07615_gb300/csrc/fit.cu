@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(G_THREADS) fit_gemm_kernel(const FitJob* __res
   gemm_tile<T>(d, blockIdx.x, ib, k0, k1, part);
 }
 
-// fit_gemm_kernel<float, STAGE> with the tiles on the tensor cores (TF32
-// operands, FP32 accumulation; same grid, split-K ranges and outputs).
-template <int STAGE>
+// fit_gemm_kernel<float, STAGE> with the tiles on the tensor cores (TF32 or
+// BF16 operands, FP32 accumulation; same grid, split-K ranges and outputs).
+template <int STAGE, bool BF16>
 __global__ void __launch_bounds__(G_THREADS) fit_gemm_tc_kernel(const FitJob* __restrict__ jobs, int L, int c,
                                                                 double* ctr, int splits, int nbm, int* status) {
   const FitJob& J = jobs[blockIdx.z];
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(G_THREADS) fit_gemm_tc_kernel(const FitJob* __
   if (ctr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
     atomicAdd(&ctr[C_FIT_GEMM], 2.0 * d.M * d.N * d.K * d.nb_hi * d.nb_lo);
   if (splits <= 1) {
-    gemm_tile_tc(d, blockIdx.x, blockIdx.y, 0, d.K, nullptr, status);
+    gemm_tile_tc<BF16>(d, blockIdx.x, blockIdx.y, 0, d.K, nullptr, status);
     return;
   }
   const int split = blockIdx.y / nbm, ib = blockIdx.y % nbm;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(G_THREADS) fit_gemm_tc_kernel(const FitJob* __
   const int kc = ((d.K + splits - 1) / splits + GB_K - 1) / GB_K * GB_K;
   const int k0 = imin(d.K, split * kc), k1 = imin(d.K, k0 + kc);
   float* part = (float*)J.x + ((size_t)split * nb + ib) * d.M * d.N;
-  gemm_tile_tc(d, blockIdx.x, ib, k0, k1, part, status);
+  gemm_tile_tc<BF16>(d, blockIdx.x, ib, k0, k1, part, status);
 }
 
 template <typename T, int STAGE>
@@ -322,7 +322,7 @@ static void set_fit_smem() {
 // ---------------------------------------------------------------- host driver
 template <typename T, int STAGE>
 static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int c,
-                        cudaStream_t st, Prof* prof, bool tc, int* d_status) {
+                        cudaStream_t st, Prof* prof, int tc, int* d_status) {
   int tiles = 1, nb = 1, kmax = 1;
   size_t elems = 1;
   for (const FitJob& j : hj) {
@@ -341,9 +341,13 @@ static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int
   dim3 grid(tiles, nb * splits, (unsigned)hj.size());
   bool launched = false;
   if constexpr (sizeof(T) == 4) {
-    if (tc) {
-      fit_gemm_tc_kernel<STAGE><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr, splits, nb,
-                                                            d_status);
+    if (tc == TC_TF32) {
+      fit_gemm_tc_kernel<STAGE, false><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr,
+                                                                   splits, nb, d_status);
+      launched = true;
+    } else if (tc == TC_BF16) {
+      fit_gemm_tc_kernel<STAGE, true><<<grid, G_THREADS, 0, st>>>(d_jobs, L, c, prof ? prof->d_ctr : nullptr,
+                                                                  splits, nb, d_status);
       launched = true;
     }
   }
@@ -359,7 +363,7 @@ static int launch_stage(const FitJob* d_jobs, const std::vector<FitJob>& hj, int
 
 template <typename T>
 int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int sweeps,
-            int* d_status, cudaStream_t st, Prof* prof, bool tc) {
+            int* d_status, cudaStream_t st, Prof* prof, int tc) {
   const int nj = (int)hj.size();
   if (nj == 0) return 0;
   double* ctr = prof ? prof->d_ctr : nullptr;
@@ -434,7 +438,7 @@ void plan_fit_job(FitJob& j, int L, size_t* env_elems, size_t* x_elems, size_t* 
   *q_elems = (q + 31) & ~(size_t)31;
 }
 
-template int run_fit<float>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, bool);
-template int run_fit<double>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, bool);
+template int run_fit<float>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, int);
+template int run_fit<double>(const FitJob*, const std::vector<FitJob>&, int, int, int*, cudaStream_t, Prof*, int);
 
 }  // namespace tn

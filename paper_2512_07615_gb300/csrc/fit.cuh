@@ -67,10 +67,12 @@ struct Prof {
   }
 };
 
-// tc: the GEMM stages on the tensor cores (tcgen05 kind::tf32; float storage only)
+// tc: the GEMM stages on SIMT cores (TC_NONE) or on the tensor cores with
+// TF32 (tcgen05 kind::tf32) or BF16 (kind::f16) operands; float storage only
+enum : int { TC_NONE = 0, TC_TF32 = 1, TC_BF16 = 2 };
 template <typename T>
 int run_fit(const FitJob* d_jobs, const std::vector<FitJob>& hj, int L, int sweeps, int* d_status,
-            cudaStream_t st, Prof* prof = nullptr, bool tc = false);
+            cudaStream_t st, Prof* prof = nullptr, int tc = TC_NONE);
 
 // ---- misc.cu
 // out[b] = <X_b, 1> for MPS refs in device memory

@@ -45,6 +45,10 @@ enum : int { PH_TERMS = 0, PH_GEMM_M = 1, PH_QR = 2, PH_JACOBI = 3, PH_SVD_OUT =
              PH_SVD64_FLOPS = 10, PH_SVD64_EXEC = 11, PH_RX_NORM = 12, PH_RX_DOT = 13, PH_RX_WAIT = 14,
              PH_RX_ANGLE = 15, PH_RX_ROT = 16, PH_J32 = 17, PH_NS = 18, PH_XV = 19, PH_SWEEPS32 = 20,
              PH_ROUNDS64 = 21, PH_COUNT = 22 };
+// Precision modes: which run the centre SVDs in FP64 (FP32 data) and which
+// put the fit's contractions on the tensor cores (0 none, 1 TF32, 2 BF16).
+inline bool prec_svd64(int p) { return p == TNLBM_MIXED || p == TNLBM_BF16; }
+inline int prec_tc(int p) { return p == TNLBM_TF32 ? 1 : p == TNLBM_BF16 ? 2 : 0; }
 static constexpr int CTR_SIZE = 32;   // >= C_COUNT + PH_COUNT
 // Householder QR with explicit Q of an m x n matrix, LAPACK-style counts
 __host__ __device__ inline double qr_flops(double m, double n) {

@@ -1,17 +1,19 @@
-// Tensor-core (tcgen05, kind::tf32) version of gemm_tile for FP32 storage:
-// the same 64 x 64 output tile of one strided GEMM descriptor, computed by
-// tcgen05.mma with TF32 operands and FP32 accumulation in tensor memory.
+// Tensor-core (tcgen05) version of gemm_tile for FP32 storage: the same
+// 64 x 64 output tile of one strided GEMM descriptor, computed by tcgen05.mma
+// with TF32 operands (kind::tf32) or BF16 operands (kind::f16, both A and B
+// BF16) and FP32 accumulation in tensor memory.
 //
-// Operands are rounded to TF32 (nearest) and staged by the CTA's threads
-// into shared memory in the K-major, no-swizzle canonical layout (core
-// matrices of 8 rows x 16 bytes;
-// LBO = 128 B between core matrices along K, SBO = (TK / 4) * 128 B between
-// 8-row groups).  The MMA shape is M = 128 (rows 64..127 of A are zero),
-// N = 64, K = 8 per instruction; one thread issues the TK / 8 instructions of
-// a K chunk and commits them to an mbarrier that all threads wait on (with
-// an iteration limit) before the chunk's shared memory is refilled.  The
-// 64 x 64 FP32 accumulator (64 TMEM columns) is read back with tcgen05.ld by
-// the warps that own TMEM lanes 0..63.
+// Operands are rounded to TF32 or BF16 (nearest) and staged by the CTA's
+// threads into shared memory in the K-major, no-swizzle canonical layout:
+// core matrices of 8 rows x 16 bytes (4 TF32 or 8 BF16 values per row),
+// LBO = 128 B between core matrices along K, SBO = 128 B times the core
+// matrices per 8-row group between 8-row groups.  The MMA shape is M = 128
+// (rows 64..127 of A are zero), N = 64, and 32 bytes of K per instruction
+// (K = 8 TF32 or 16 BF16); one thread issues the instructions of a K chunk
+// and commits them to an mbarrier that all threads wait on (with an
+// iteration limit) before the chunk's shared memory is refilled.  The 64 x 64
+// FP32 accumulator (64 TMEM columns) is read back with tcgen05.ld by the
+// warps that own TMEM lanes 0..63.
 #pragma once
 
 #include <stdint.h>
@@ -35,9 +37,19 @@ __device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr, uint32_t lbo, uint32
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor, kind::tf32: D F32, A and B TF32, both K-major.
-__host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// Instruction descriptor: D F32 (bits 4-5), A and B format (bits 7-9, 10-12:
+// TF32 = 2 under kind::tf32, BF16 = 1 under kind::f16), both K-major, N / 8
+// (bits 17-22), M / 16 (bits 24-28).
+__host__ __device__ constexpr uint32_t tc_idesc(int m, int n, bool bf16 = false) {
+  return (1u << 4) | ((bf16 ? 1u : 2u) << 7) | ((bf16 ? 1u : 2u) << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+// FP32 -> BF16 bits, round to nearest even
+__device__ __forceinline__ uint16_t tc_bf16(float x) {
+  uint16_t r;
+  asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(r) : "f"(x));
+  return r;
 }
 
 // FP32 -> TF32, round to nearest (the MMA itself would drop the low 13 bits,
@@ -67,10 +79,15 @@ __device__ __forceinline__ void tc_ld16(uint32_t addr, uint32_t (&r)[16]) {
 
 // gemm_tile on the tensor cores (blockDim.x == G_THREADS == 256).  A timed-out
 // wait sets ST_TIMEOUT in *status and leaves the tile unwritten.
+template <bool BF16>
 __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, int k_begin, int k_end, float* part,
                                              int* status) {
+  // the same bytes for either operand type: 128 (A) or 64 (B) rows of TC_K
+  // values (TF32: 4 bytes each; BF16: the first half of the buffer)
   __shared__ __align__(1024) float sA[128 * TC_K];
   __shared__ __align__(1024) float sB[64 * TC_K];
+  uint16_t* hA = (uint16_t*)sA;
+  uint16_t* hB = (uint16_t*)sB;
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
@@ -84,7 +101,10 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   float* C = (float*)d.C + hi * d.c_bh + lo * d.c_bl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mbar = tc_smem(&s_mbar);
-  for (int e = tid; e < 64 * TC_K; e += blockDim.x) sA[64 * TC_K + e] = 0.f;   // rows 64..127
+  for (int e = tid; e < 64 * TC_K; e += blockDim.x) {                             // rows 64..127
+    if constexpr (BF16) hA[64 * TC_K + e] = 0;
+    else sA[64 * TC_K + e] = 0.f;
+  }
   if (tid == 0) {
     s_fail = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar));
@@ -99,8 +119,9 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t idesc = tc_idesc(128, 64);
-  const uint32_t sbo = (TC_K / 4) * 128;
+  const uint32_t idesc = tc_idesc(128, 64, BF16);
+  constexpr int VPR = BF16 ? 8 : 4;                // values per 16-byte core-matrix row
+  const uint32_t sbo = (TC_K / VPR) * 128;
   uint32_t parity = 0;
   bool issued = false;
   for (int k0 = k_begin; k0 < k_end; k0 += TC_K) {
@@ -109,27 +130,37 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
       int mm, kk;
       if (d.a_cs == 1) { mm = e / TC_K; kk = e % TC_K; } else { kk = e / 64; mm = e % 64; }
       const int gm = m0 + mm, gk = k0 + kk;
-      sA[((mm >> 3) * (TC_K / 4) + (kk >> 2)) * 32 + (mm & 7) * 4 + (kk & 3)] =
-          (gm < d.M && gk < k_end) ? tc_tf32(A[gm * d.a_rs + gk * d.a_cs]) : 0.f;
+      const float v = (gm < d.M && gk < k_end) ? A[gm * d.a_rs + gk * d.a_cs] : 0.f;
+      const int at = ((mm >> 3) * (TC_K / VPR) + kk / VPR) * (8 * VPR) + (mm & 7) * VPR + kk % VPR;
+      if constexpr (BF16) hA[at] = tc_bf16(v);
+      else sA[at] = tc_tf32(v);
     }
     for (int e = tid; e < 64 * TC_K; e += blockDim.x) {
       int nn, kk;
       if (d.b_cs == 1) { kk = e / 64; nn = e % 64; } else { nn = e / TC_K; kk = e % TC_K; }
       const int gn = n0 + nn, gk = k0 + kk;
-      sB[((nn >> 3) * (TC_K / 4) + (kk >> 2)) * 32 + (nn & 7) * 4 + (kk & 3)] =
-          (gk < k_end && gn < d.N) ? tc_tf32(B[gk * d.b_rs + gn * d.b_cs]) : 0.f;
+      const float v = (gk < k_end && gn < d.N) ? B[gk * d.b_rs + gn * d.b_cs] : 0.f;
+      const int at = ((nn >> 3) * (TC_K / VPR) + kk / VPR) * (8 * VPR) + (nn & 7) * VPR + kk % VPR;
+      if constexpr (BF16) hB[at] = tc_bf16(v);
+      else sB[at] = tc_tf32(v);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int s = 0; s < TC_K / 8; ++s) {
+      // 32 bytes of K (two core matrices) per instruction
+      for (int s = 0; s < TC_K / (2 * VPR); ++s) {
         const uint64_t da = tc_sdesc(tc_smem(sA) + s * 256, 128, sbo);
         const uint64_t db = tc_sdesc(tc_smem(sB) + s * 256, 128, sbo);
         const uint32_t acc = (issued || s > 0) ? 1u : 0u;
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        if constexpr (BF16)
+          asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                       :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+        else
+          asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                       :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar)
                    : "memory");

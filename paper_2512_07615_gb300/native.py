@@ -8,7 +8,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtnlbm.so")
 
-FP64, FP32, TF32, MIXED = 0, 1, 2, 3
+FP64, FP32, TF32, MIXED, BF16 = 0, 1, 2, 3, 4
 D3Q19, D3Q15 = 19, 15
 FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
 HADAMARD_FIT, HADAMARD_EXACT, HADAMARD_ZIPUP = 0, 1, 2

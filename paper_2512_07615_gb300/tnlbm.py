@@ -8,7 +8,8 @@ import torch
 
 from . import native as nat
 
-_DT = {nat.FP64: torch.float64, nat.FP32: torch.float32, nat.TF32: torch.float32, nat.MIXED: torch.float32}
+_DT = {nat.FP64: torch.float64, nat.FP32: torch.float32, nat.TF32: torch.float32, nat.MIXED: torch.float32,
+       nat.BF16: torch.float32}
 
 
 def mps_size(L, cap):

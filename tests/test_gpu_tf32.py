@@ -1,10 +1,12 @@
 """Tensor-core contractions (precision TNLBM_TF32: FP32 storage, the fit's
 GEMM stages as tcgen05.mma kind::tf32 with FP32 accumulation in tensor
-memory).  TF32 keeps 10 mantissa bits, so each contraction carries a
-relative error of ~1e-3 of its terms; the gates are the 1e-3 level of the
-reduced-precision path: the fit against the exact product when the candidate
-bond suffices and against the FP32 fit, and the step against the FP64 dense
-oracle (and that no tile timed out)."""
+memory; TNLBM_BF16: the same stages as kind::f16 with BF16 operands, with the
+mixed mode's FP64 centre SVDs).  TF32 keeps 10 mantissa bits, so each
+contraction carries a relative error of ~1e-3 of its terms; the gates are the
+1e-3 level of the reduced-precision path: the fit against the exact product
+when the candidate bond suffices and against the FP32 fit, and the step
+against the FP64 dense oracle (and that no tile timed out).  BF16 keeps 8
+bits: the fit itself is gated at 2e-2, the step at 1e-3."""
 import numpy as np
 import pytest
 
@@ -113,3 +115,57 @@ def test_tf32_fit_with_split_k_tracks_fp32(tl):
     a_tc = _fit(tl, B, C, 32, 2)
     assert max(x.shape[2] for x in B) == 32 and max(x.shape[2] for x in C) >= 16
     assert rel(M.to_tensor(a_tc), M.to_tensor(a32)) < 3e-3
+
+
+# ---------------------------------------------------------------- BF16 operands (TNLBM_BF16)
+# BF16 keeps 8 mantissa bits (relative rounding 2^-9 ~ 2e-3 per operand); the
+# products are summed in FP32 in tensor memory, so a contraction carries a
+# relative error of a few 1e-3 of its terms.
+
+def test_bf16_fit_exact_bond_and_close_to_fp32(tl):
+    """As the TF32 case: candidate bond 24 holds the product on 12 sites."""
+    L = 12
+    B = synth.random_mps(L, synth.feasible_ranks(L, 24), 11)
+    C = M.rank1([np.random.default_rng(k).uniform(0.5, 1.5, 2) for k in range(L)])
+    C = M.round_mps(M.add(C, M.scale(C, 0.5)), 4, 0.0)
+    exact = M.to_tensor(B) * M.to_tensor(C)
+    a32 = _fit(tl, B, C, 24, 1)
+    abf = _fit(tl, B, C, 24, 4)
+    e_ex, e_32 = rel(M.to_tensor(abf), exact), rel(M.to_tensor(abf), M.to_tensor(a32))
+    print("bf16 fit, exact bond: vs exact %.3e, vs fp32 fit %.3e" % (e_ex, e_32))
+    assert e_ex < 2e-2 and e_32 < 2e-2                   # measured 1.3e-2
+
+
+def test_bf16_fit_with_split_k_tracks_fp32(tl):
+    n = 5
+    B = M.tt_svd(q.encode(smooth(n, 5, n_modes=16)), 32, 0.0)
+    C = M.tt_svd(q.encode(smooth(n, 6, n_modes=6)), 16, 0.0)
+    a32 = _fit(tl, B, C, 32, 1)
+    abf = _fit(tl, B, C, 32, 4)
+    e = rel(M.to_tensor(abf), M.to_tensor(a32))
+    print("bf16 fit, split-K: vs fp32 fit %.3e" % e)
+    assert e < 2e-2                                       # measured 1.1e-2
+
+
+def test_bf16_step_vs_fp64_dense(tl):
+    """The TF32 step case with TNLBM_BF16 (BF16 fit contractions, FP64 centre
+    SVDs): against the FP64 dense Taylor step after 3 steps, mass held, device
+    status clean."""
+    modes = synth.fourier_modes(3, 7, kmax=2, amp_rho=1e-3, amp_u=1e-2)
+    kw = dict(tau=0.8, periodic=(1, 1, 0), force=(1e-5, 0.0, 0.0), chi_max=16, eps=1e-9)
+    sim = tl.Sim(3, precision=4, hadamard=0, modes=modes, conserve_mass=True, **kw)
+    rho_start, _ = sim.macroscopic()
+    lat = lattice.D3Q19
+    cfg = ml.Config(3, lat, 0.8, force=kw["force"], periodic=kw["periodic"], chi_max=16, eps=1e-9, hadamard="exact")
+    fd = ml.to_dense_populations(ml.initial_perturbed(cfg, modes))
+    for _ in range(3):
+        fd = ld.step(fd, lat, 0.8, kw["force"], None, kw["periodic"], "taylor")
+    sim.step(3)
+    rho, u = sim.macroscopic()
+    _, ud = ld.velocity_out(lat, fd, kw["force"])
+    err = rel_l2(u, ud)
+    print("bf16 step vs fp64 dense: rel-L2(u) = %.3e" % err)
+    assert err <= 1e-3                                    # measured 6.0e-4
+    assert abs(rho.sum() - rho_start.sum()) / rho_start.sum() <= 1e-6
+    assert sim.stats()["status"] == 0
+    sim.close()
