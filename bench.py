@@ -595,6 +595,16 @@ def main():
                          "svd64_executed_tflops": ph["svd64_exec_flops"] / (jac_ms / 1e3) / 1e12 if jac_ms else None})
         if peak and jac_ms:
             roofline["svd64_executed_frac"] = roofline["svd64_executed_tflops"] / peak
+        if w["precision"] == 3 and w.get("geometry") == "spheres":
+            # DRAM bytes of one rounding launch: the ncu capture of this kernel
+            # on the porous 64^3 workload (1.698 MB for a launch of 4 jobs,
+            # profiles/round_kernel_porous64_mixed.md) scaled by the jobs of
+            # an average launch of this run
+            per_job = 1.698e6 / 4.0
+            roofline["traffic"] = per_job * st["round_jobs_per_step"] / max(rd["launches"], 1)
+            roofline["traffic_note"] = ("bytes per launch: dram__bytes_read + write of the porous 64^3 capture "
+                                        "(0.42 MB per job) x jobs per launch; the kernel is FP64-latency bound, "
+                                        "not DRAM bound")
     else:
         peak = peaks.get("fp32_simt_tflops")
         ach = rd["flops"] / (rd["ms"] / 1e3) / 1e12 if rd["ms"] > 0 else 0.0
