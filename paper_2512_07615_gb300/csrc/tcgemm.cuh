@@ -7,13 +7,15 @@
 // threads into shared memory in the K-major, no-swizzle canonical layout:
 // core matrices of 8 rows x 16 bytes (4 TF32 or 8 BF16 values per row),
 // LBO = 128 B between core matrices along K, SBO = 128 B times the core
-// matrices per 8-row group between 8-row groups.  The MMA shape is M = 128
-// (rows 64..127 of A are zero), N = 64, and 32 bytes of K per instruction
-// (K = 8 TF32 or 16 BF16); one thread issues the instructions of a K chunk
-// and commits them to an mbarrier that all threads wait on (with an
-// iteration limit) before the chunk's shared memory is refilled.  The 64 x 64
-// FP32 accumulator (64 TMEM columns) is read back with tcgen05.ld by the
-// warps that own TMEM lanes 0..63.
+// matrices per 8-row group between 8-row groups.  The MMA shape is M = 128,
+// N = 64, and 32 bytes of K per instruction (K = 8 TF32 or 16 BF16): one CTA
+// computes a 128 x 64 output tile (two of the 64-row tiles of the SIMT grid;
+// the CTAs of the grid's odd row tiles have nothing to do and return).  One
+// thread issues the instructions of a K chunk and commits them to an mbarrier
+// that all threads wait on (with an iteration limit) before the chunk's
+// shared memory is refilled.  The 128 x 64 FP32 accumulator (64 TMEM columns,
+// 128 lanes) is read back with tcgen05.ld: warp w reads lanes
+// 32 (w mod 4) .. + 31 and columns 32 (w / 4) .. + 31.
 #pragma once
 
 #include <stdint.h>
@@ -93,7 +95,7 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   __shared__ int s_fail;
   const int tn = (d.N + GB_N - 1) / GB_N;
   const int tm_i = tile / tn, tn_i = tile % tn;
-  const int m0 = tm_i * GB_M, n0 = tn_i * GB_N;
+  const int m0 = tm_i * 128, n0 = tn_i * GB_N;     // 128-row tiles on the 64-row grid
   if (m0 >= d.M || ib >= d.nb_hi * d.nb_lo) return;       // uniform over the CTA
   const int hi = ib / d.nb_lo, lo = ib % d.nb_lo;
   const float* A = (const float*)d.A + hi * d.a_bh + lo * d.a_bl;
@@ -101,10 +103,6 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   float* C = (float*)d.C + hi * d.c_bh + lo * d.c_bl;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t mbar = tc_smem(&s_mbar);
-  for (int e = tid; e < 64 * TC_K; e += blockDim.x) {                             // rows 64..127
-    if constexpr (BF16) hA[64 * TC_K + e] = 0;
-    else sA[64 * TC_K + e] = 0.f;
-  }
   if (tid == 0) {
     s_fail = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mbar));
@@ -125,10 +123,10 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   uint32_t parity = 0;
   bool issued = false;
   for (int k0 = k_begin; k0 < k_end; k0 += TC_K) {
-    // A rows 0..63 and B (N x K, K-major) into the core-matrix layout
-    for (int e = tid; e < 64 * TC_K; e += blockDim.x) {
+    // A rows 0..127 and B (N x K, K-major) into the core-matrix layout
+    for (int e = tid; e < 128 * TC_K; e += blockDim.x) {
       int mm, kk;
-      if (d.a_cs == 1) { mm = e / TC_K; kk = e % TC_K; } else { kk = e / 64; mm = e % 64; }
+      if (d.a_cs == 1) { mm = e / TC_K; kk = e % TC_K; } else { kk = e / 128; mm = e % 128; }
       const int gm = m0 + mm, gk = k0 + kk;
       const float v = (gm < d.M && gk < k_end) ? A[gm * d.a_rs + gk * d.a_cs] : 0.f;
       const int at = ((mm >> 3) * (TC_K / VPR) + kk / VPR) * (8 * VPR) + (mm & 7) * VPR + kk % VPR;
@@ -174,7 +172,7 @@ __device__ __forceinline__ void gemm_tile_tc(const GDesc& d, int tile, int ib, i
   }
   if (s_fail) {
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
-  } else if ((warp & 3) < 2) {
+  } else {
     // rows 32 (warp & 3) + lane, columns 32 (warp >> 2) .. + 31
     const int row = 32 * (warp & 3) + lane, cbase = 32 * (warp >> 2);
     const int gm = m0 + row;
