@@ -407,83 +407,64 @@ __device__ __forceinline__ void renorm64(float cf, float sf, double& c, double& 
   s = s0 * h;
 }
 
-// Rotation of a pair with norms al, be and inner product g (exchanged values,
-// identical in every CTA): false if the pair counts as orthogonal
+// Rotation of a pair with norms al, be and inner product g (exchanged FP64
+// values, identical in every CTA): false if the pair counts as orthogonal
 // (g^2 <= tol2 al be) or a column is negligible.  t = tan(theta) is
-// Rutishauser's root of the FP32 quotient zeta = (be - al) / (2 g) (for
-// S = double the difference is taken in FP64, and a quotient outside the
-// FP32 range is formed in FP64, with t = 1 / (2 zeta) once |zeta| > 1e18).
-// c = (1 + t^2)^(-1/2) and s = c t are FP32; for S = double (and for every
-// rotation of V, see renorm64) they are taken renormalised in FP64, so that
-// each rotation is orthogonal to FP64 rounding; for S = float W turns by the
-// FP32 (c, s).  The new norms are al - t g and be + t g (exact for the exact
-// root; recomputed every sweep).
-template <typename S>
-__device__ __forceinline__ bool rows_angle(S al, S be, S g, S tol2, S& cw, S& sw, S& na, S& nb, float& rel2) {
-  S amin;
-  if constexpr (sizeof(S) == 8) amin = 1e-250;
-  else amin = 1e-30f;
-  const S gg = g * g, ab = al * be;
-  if (g == (S)0 || !(al > amin) || !(be > amin) || gg <= tol2 * ab) return false;
-  rel2 = (float)gg / (float)ab;                         // g^2 / (al be); +inf if al be leaves the FP32 range
-  const S d = be - al;
-  float tf;
-  S t;
+// Rutishauser's root of the FP32 quotient zeta = (be - al) / (2 g) of the
+// FP64 difference (a quotient outside the FP32 range is formed in FP64, with
+// t = 1 / (2 zeta) once |zeta| > 1e18).  (c, s) = (1, t) (1 + t^2)^(-1/2)
+// orthogonal to FP64 rounding: for |t| < 2^-14 by the series c = 1 - t^2/2,
+// s = t c; else the FP32 (c, s) renormalised in FP64 (renorm64).  The new
+// norms are al - t g and be + t g (exact for the exact root; recomputed every
+// sweep); rel2 = g^2 / (al be) for the stopping rule.
+__device__ __forceinline__ bool rows_angle(double al, double be, double g, double tol2, double& cw, double& sw,
+                                           double& na, double& nb, float& rel2) {
+  const double gg = g * g, ab = al * be;
+  if (g == 0.0 || !(al > 1e-250) || !(be > 1e-250) || gg <= tol2 * ab) return false;
+  rel2 = (float)gg / (float)ab;                         // +inf if al be leaves the FP32 range
+  const double d = be - al;
+  float tf = 0.f;
+  double t;
   bool tiny = false;
-  if constexpr (sizeof(S) == 8) {
-    if (fabs(d) > 1e18 * fabs(g) || fabs(g) < 1e-30) {
-      const double zd = d / (2.0 * g);                  // outside the FP32 range: FP64 (rare)
-      if (fabs(zd) > 1e18) {
-        t = 0.5 / zd;
-        tiny = true;
-      } else {
-        const float z = (float)zd;
-        tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
-        t = (double)tf;
-      }
+  if (fabs(d) > 1e18 * fabs(g) || fabs(g) < 1e-30) {
+    const double zd = d / (2.0 * g);                    // outside the FP32 range: FP64 (rare)
+    if (fabs(zd) > 1e18) {
+      t = 0.5 / zd;
+      tiny = true;
     } else {
-      const float z = (float)d / (2.f * (float)g);
+      const float z = (float)zd;
       tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
       t = (double)tf;
     }
   } else {
-    const float z = d / (2.f * g);
+    const float z = (float)d / (2.f * (float)g);
     tf = copysignf(1.f / (fabsf(z) + sqrtf(fmaf(z, z, 1.f))), z);
-    if (tf == 0.f) return false;                        // below the FP32 range: nothing to rotate
-    t = tf;
+    t = (double)tf;
   }
   if (tiny) {
-    cw = (S)1;                                          // 1 + t^2 rounds to 1 for |t| < 1e-18
+    cw = 1.0;                                           // 1 + t^2 rounds to 1 for |t| < 1e-18
     sw = t;
-  } else if (sizeof(S) == 8 && fabsf(tf) < 6.1035156e-05f) {
-    // |t| < 2^-14 (most rotations of the FP64 sweeps): c = 1 - t^2/2 and
-    // s = t c give c^2 + s^2 = 1 - 3 t^4 / 4 + ..., orthogonal to FP64 rounding
-    const double td = (double)tf;
-    const double c = fma(-0.5 * td, td, 1.0);
-    cw = (S)c;
-    sw = (S)(td * c);
+  } else if (fabsf(tf) < 6.1035156e-05f) {
+    // c^2 + s^2 = 1 - 3 t^4 / 4 + ...: orthogonal to FP64 rounding
+    const double c = fma(-0.5 * t, t, 1.0);
+    cw = c;
+    sw = t * c;
   } else {
     const float cf = rsqrtf(fmaf(tf, tf, 1.f)), sf = cf * tf;
-    if constexpr (sizeof(S) == 8) {
-      renorm64(cf, sf, cw, sw);
-    } else {
-      cw = cf;
-      sw = sf;
-    }
+    renorm64(cf, sf, cw, sw);
   }
   na = al - t * g;
   nb = be + t * g;
   return true;
 }
 
-// Cyclic one-sided Jacobi sweeps (round-robin order) on the cluster's rows of
-// W (type S: the arithmetic of the inner products, norms and angles) and of
-// V (FP64); nrot counts rotations.  Per round: each CTA's parts of the pair
-// inner products go to every CTA, four lanes per pair add them in rank order,
-// lane 0 takes the angle, and every CTA rotates its rows of W and V.
+// Cyclic one-sided Jacobi sweeps (round-robin order) on the cluster's FP64
+// rows of W and V; nrot counts rotations.  Per round: each CTA's parts of the
+// pair inner products go to every CTA, four lanes per pair add them in rank
+// order, lane 0 takes the angle, and every CTA rotates its rows of W and V.
 // Stopping rule: a sweep that rotates nothing (every pair within the
-// tolerance), or, for FP64 rows, a sweep whose largest relative inner
-// product g^2 / (al be) was below (5e-9)^2 -- Jacobi converges quadratically,
+// tolerance), or a sweep whose largest relative inner product
+// g^2 / (al be) was below (5e-9)^2 -- Jacobi converges quadratically,
 // so its rotations leave every pair below ~(5e-9)^2 ncol plus the FP32 angle's
 // residual 1.2e-7 x 5e-9, under the tolerance 16 eps_64 sqrt(len) >= 5e-15,
 // and the confirming sweep is skipped.  Every CTA sees the same values, so
@@ -493,6 +474,7 @@ template <typename S>
 __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* wa, S* Wl, double* Vl, int ncol,
                            int li, int vi, int maxsw, S tol2, unsigned* nrot, double* phase_acc, bool* converged,
                            int* rounds_out = nullptr) {
+  static_assert(sizeof(S) == 8, "the cluster sweeps run on FP64 rows");
   __shared__ float s_mrel[32];
   RxClock rx(phase_acc);
   unsigned q = 0;                                  // rounds so far (exchange buffer parity)
@@ -506,20 +488,14 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
   *converged = true;
   if (ncol < 2) return 0;
   *converged = false;
-  // rotation of this CTA's rows of V by round rnd's pairs (FP64, renormalised)
+  // rotation of this CTA's rows of V by round rnd's pairs
   auto rotate_v = [&](int rnd) {
     for (int idx = threadIdx.x; idx < npairs * vi; idx += blockDim.x) {
       const int p = idx / vi, ii = idx - p * vi;
       if (!pfl[p]) continue;
       int a, b;
       rr_pair(rnd, p, np, a, b);
-      double cs, sn;
-      if constexpr (sizeof(S) == 8) {
-        cs = pcw[p];
-        sn = psw[p];
-      } else {
-        renorm64(pcw[p], psw[p], cs, sn);
-      }
+      const double cs = pcw[p], sn = psw[p];
       double* pa = Vl + (size_t)a * R.lv + ii;
       double* pb = Vl + (size_t)b * R.lv + ii;
       const double u = *pa, w = *pb;
@@ -553,7 +529,7 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
         if (b < ncol) {
           S cw, sw, na, nb;
           float rel2 = 0.f;
-          if (rows_angle<S>(nrm[a], nrm[b], g, tol2, cw, sw, na, nb, rel2)) {
+          if (rows_angle(nrm[a], nrm[b], g, tol2, cw, sw, na, nb, rel2)) {
             mrel = fmaxf(mrel, rel2);
             nrm[a] = na;
             nrm[b] = nb;
@@ -590,16 +566,14 @@ __device__ int rows_sweeps(ClusterCtx& cc, const RowsLayout& R, unsigned char* w
     }
     if (cc.dead) break;
     if (!any) { *converged = true; break; }
-    if constexpr (sizeof(S) == 8) {
-      // the sweep's largest relative inner product (the same in every CTA)
-      for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
-      if ((threadIdx.x & 31) == 0) s_mrel[threadIdx.x >> 5] = mrel;
-      __syncthreads();
-      float m = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_mrel[w]);
-      __syncthreads();
-      if (m < 2.5e-17f) { *converged = true; ++sweep; break; }
-    }
+    // the sweep's largest relative inner product (the same in every CTA)
+    for (int o = 16; o > 0; o >>= 1) mrel = fmaxf(mrel, __shfl_xor_sync(0xffffffffu, mrel, o));
+    if ((threadIdx.x & 31) == 0) s_mrel[threadIdx.x >> 5] = mrel;
+    __syncthreads();
+    float m = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_mrel[w]);
+    __syncthreads();
+    if (m < 2.5e-17f) { *converged = true; ++sweep; break; }
   }
   if (phase_acc && threadIdx.x == 0) phase_acc[PH_ROUNDS64] += rounds;
   if (rounds_out) *rounds_out = rounds;
