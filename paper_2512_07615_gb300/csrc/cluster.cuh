@@ -211,13 +211,6 @@ __device__ __forceinline__ void cl_xchg_send(const ClusterCtx& c, const double* 
                : "memory");
 }
 
-// One float into CTA `rank`'s copy of *p, counted on its current exchange.
-__device__ __forceinline__ void cl_xchg_send(const ClusterCtx& c, const float* p, unsigned rank, float v) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
-               ::"r"(cl_map(p, rank)), "r"(__float_as_uint(v)), "r"(cl_map(&c.sh->xbar[c.xe & 1], rank))
-               : "memory");
-}
-
 // Wait (thread 0 polls, bounded by the wait limit in SM clocks) until all
 // bytes of this exchange have arrived; then the CTA meets.  False (uniformly)
 // once this CTA has given up.
