@@ -20,7 +20,9 @@ Prints one JSON line (rank 0):
   roofline     the rounding kernel (the dominant one) against its peak
   cpu_baseline the CPU oracle timed on one whole step of the timed state
   clocks       nvidia-smi samples taken during the timed region
-  batched      eight 64^3 simulations stepped in one graph (FP32)
+  batched      eight 64^3 simulations stepped in one graph (mixed precision,
+               cluster sizes tuned per level) against the same eight stepped
+               one after another, in mixed precision and in plain FP64
 
 --impl reference times the CPU oracle instead (the reference arm): one oracle
 step of the workload's start is recorded call by call (roundings and products
@@ -287,43 +289,57 @@ def batch_configs(precision=1, chis=BATCH_CHIS):
                         chi_mask=chi, eps_mask=1e-8, force=(1e-5, 0, 0), chi_max=chi, eps=1e-7,
                         precision=precision, hadamard=0, sweeps=2,
                         modes=synth.fourier_modes(15, 10 + i, kmax=3, amp_rho=1e-3, amp_u=1e-3),
-                        conserve_mass=precision == 1))
+                        conserve_mass=precision != 0))
     return out
 
 
-def batched_measurement(warmup=2, steps=2):
-    """The batched workload: eight simulations stepped in one graph against the
-    same eight stepped one after another, and against one plain FP64
-    full-SVD simulation of the largest chi."""
+def batched_measurement(precision=3, warmup=1, steps=2, tune=True):
+    """The batched workload: eight 64^3 simulations stepped in one graph, with
+    the cluster sizes of the occupancy rule and after the per-level tuner,
+    against the same eight stepped one after another in this precision and in
+    the plain FP64 full-SVD path (one untimed step each, then one timed)."""
     import paper_2512_07615_gb300 as tl
     N3 = 64 ** 3
-    cfgs = batch_configs()
+    cfgs = batch_configs(precision)
     b = tl.Batch(cfgs)
     info = b.info()
+    sizes0, jobs = b.clusters()
+    b.step(1)
+    ms0 = b.step_timed(1)
+    tuned = None
+    if tune and precision in (0, 3, 4):
+        t = time.perf_counter()
+        r = b.tune_clusters(reps=1)
+        tuned = {"tune_s": round(time.perf_counter() - t, 2), "sizes": r["sizes"], "occupancy_sizes": sizes0,
+                 "jobs_per_level": jobs}
     b.step(warmup)
     ms = b.step_timed(steps) / steps
     b.close()
-    seq = 0.0
-    for c in cfgs:
-        c = dict(c)
-        n = c.pop("n_per_axis")
-        s = tl.Sim(n, **c)
-        s.step(1)
-        seq += s.step_timed(1)
-        s.close()
-    c = dict(batch_configs(precision=0)[2])
-    n = c.pop("n_per_axis")
-    s = tl.Sim(n, **c)
-    s.step(1)
-    ms64 = s.step_timed(1)
-    s.close()
-    return {"workload": "batched8_porous64: eight 64^3 sphere packs (seeds 0-7), chi %s, eps 1e-7, FP32"
-                        % "/".join(map(str, BATCH_CHIS)),
-            "value": len(cfgs) * N3 / (ms * 1e3), "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+
+    def alone(prec):
+        tot = 0.0
+        for c in batch_configs(prec):
+            c = dict(c)
+            n = c.pop("n_per_axis")
+            s = tl.Sim(n, **c)
+            s.step(1)
+            tot += s.step_timed(1)
+            s.close()
+        return tot
+
+    seq = alone(precision)
+    seq64 = alone(0) if precision != 0 else seq
+    cells = len(cfgs) * N3
+    return {"workload": "batched8_porous64: eight 64^3 sphere packs (seeds 0-7), chi %s, eps 1e-7, %s"
+                        % ("/".join(map(str, BATCH_CHIS)), PREC_NAME[precision]),
+            "value": cells / (ms * 1e3), "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
             "warmup": warmup, "launches_per_step": info["launches_per_step"],
             "jobs_per_step": info["jobs_per_step"],
-            "unbatched_value": len(cfgs) * N3 / (seq * 1e3), "unbatched_ms_per_round": seq,
-            "fp64_unbatched_full_svd_value": N3 / (ms64 * 1e3), "fp64_chi": cfgs[2]["chi_max"]}
+            "occupancy_rule_value": cells / (ms0 * 1e3), "occupancy_rule_ms_per_step": ms0,
+            "cluster_tuning": tuned,
+            "unbatched_value": cells / (seq * 1e3), "unbatched_ms_per_round": seq,
+            "fp64_unbatched_full_svd_value": cells / (seq64 * 1e3), "fp64_unbatched_ms_per_round": seq64,
+            "vs_fp64_unbatched": seq64 / ms}
 
 
 MIXED_SIZES = (6, 7, 8, 6, 7, 6, 8, 7)
@@ -453,6 +469,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-precision", choices=sorted(PREC), default="mixed",
+                    help="precision of the batched eight-simulation leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the occupancy rule's cluster sizes (no per-level tuning)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison (vs_baseline, rel_l2_u)")
     ap.add_argument("--precision", choices=sorted(PREC), default=None,
                     help="override the workload's precision (mixed: FP32 storage and contractions, FP64 SVD)")
@@ -546,6 +566,14 @@ def main():
     t0 = time.time()
     sim = make_sim(w, solid, modes)
     setup_s = time.time() - t0
+    tuning = None
+    if not args.no_tune and w["precision"] in (0, 3, 4):
+        # per-level cluster sizes measured once before the timed steps (one
+        # eager step without its final copy: the state is unchanged)
+        sizes0, _ = sim.clusters()
+        t0 = time.time()
+        r = sim.tune_clusters(reps=1)
+        tuning = {"tune_s": round(time.time() - t0, 2), "sizes": r["sizes"], "occupancy_sizes": sizes0}
     rho_start, _ = sim.macroscopic()
     mass_start = float(rho_start.sum())
     sim.step(args.warmup)
@@ -650,7 +678,7 @@ def main():
 
     batched = None
     if rank == 0 and not args.no_batched and args.workload == "porous128":
-        batched = batched_measurement()
+        batched = batched_measurement(PREC[args.batched_precision], tune=not args.no_tune)
     batched_mixed = None
     if rank == 0 and args.batched_mixed:
         batched_mixed = mixed_batch_measurement()
@@ -676,7 +704,7 @@ def main():
                "gpu_launches": st["gpu_launches_per_step"] * args.steps,
                "bonds": {"max": st["max_bond"], "mean": round(st["mean_bond"], 2)},
                "rounding_launch": {"jobs_per_step": st["round_jobs_per_step"], "ctas_per_step": st["round_ctas_per_step"],
-                                   "max_cluster": st["max_cluster"]},
+                                   "max_cluster": st["max_cluster"], "cluster_tuning": tuning},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
                "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,

@@ -231,6 +231,43 @@ int tnlbm_set_limits(tnlbm_sim *s, int jacobi_max_sweeps, long long wait_limit_n
  * the k launches in *ms (CUDA events on the simulation's stream). */
 int tnlbm_step_timed(tnlbm_sim *s, int k, double *ms);
 
+/* ------------------------------------------------------------------ cluster sizes
+ * Each dependency level of a step is one rounding launch.  In TNLBM_FP64,
+ * TNLBM_MIXED and TNLBM_BF16 a job of that launch runs on a thread-block
+ * cluster of P CTAs (1 <= P <= TNLBM_CLUSTER_MAX) that share its FP64 centre
+ * SVDs.  tnlbm_create picks P per level from occupancy (the largest size at
+ * which every job of the level is resident at once, capped by
+ * tnlbm_config.max_cluster); these calls read, set or measure it. */
+enum { TNLBM_CLUSTER_MAX = 16 };
+
+/* Per-level cluster sizes: clusters[l] (0 for a level without roundings) and
+ * jobs[l] (the rounding jobs of level l) for l < min(cap, levels); either
+ * array may be NULL; *nlevels (may be NULL) = the number of levels.  Host
+ * only. */
+int tnlbm_clusters(tnlbm_sim *s, int *clusters, int *jobs, int cap, int *nlevels);
+
+/* Sets the cluster size of every level with roundings from
+ * clusters[0..nlevels) (nlevels must equal the level count; entries of levels
+ * without roundings are ignored) and re-captures the step's graph.  Each size
+ * is 1..16 and fits on the device; FP32 and TF32 simulations take 1 only.
+ * Otherwise TNLBM_E_ARG with nothing changed.  Synchronous. */
+int tnlbm_set_clusters(tnlbm_sim *s, const int *clusters, int nlevels);
+
+/* Measures the cluster size of every level.  Runs one step eagerly, level by
+ * level, and times each rounding launch (CUDA events; the minimum of reps >= 1
+ * launches) at P = 16, 8, 4, 2, 1 and at the level's current size, among the
+ * sizes <= tnlbm_config.max_cluster that fit on the device, going down until
+ * a size is 1.5x slower than the best so far.  Each level keeps its fastest
+ * size (the current one unless another is 2 % faster); the graph is then
+ * re-captured.  The step's copy into the populations (and the mass correction
+ * before it) is left out: the populations, the step count and the total
+ * discarded weight are unchanged.  ms (may be NULL; ms_cap doubles):
+ * ms[l * (TNLBM_CLUSTER_MAX + 1) + P] = level l's launch time at P CTAs per
+ * job in ms, -1 where not timed.  FP32 / TF32 simulations time nothing.  Not
+ * allowed once the learned rounding is configured (TNLBM_E_ARG); a failing
+ * rounding returns its code and keeps the old sizes.  Synchronous. */
+int tnlbm_tune_clusters(tnlbm_sim *s, int reps, double *ms, int ms_cap);
+
 /* Kernel classes reported by tnlbm_profile_step (array index). */
 enum { TNLBM_K_ROUND = 0, TNLBM_K_FIT_GEMM = 1, TNLBM_K_FIT_QR = 2, TNLBM_K_FIT_MISC = 3,
        TNLBM_K_RHO0 = 4, TNLBM_K_COPY = 5, TNLBM_K_ZIPUP = 6, TNLBM_K_COUNT = 7 };
@@ -380,12 +417,14 @@ int tnlbm_mask_product(int precision, int n_outer, const void *outer_dense,
                        void *stream);
 
 /* ------------------------------------------------------------------ batched simulations
- * Several independent simulations (same n_per_axis, precision and fit sweeps;
- * lattice, geometry, walls, tau, force, chi, eps and start may differ) stepped
- * together: each dependency level of the step (Sec. 3.2) launches the
- * roundings and fits of that level of every simulation at once, and one CUDA
- * graph holds the whole batched step.  The paper runs one simulation at a
- * time; results are bitwise those of the simulations stepped alone. */
+ * Several independent simulations (same precision and fit sweeps; lattice
+ * size, velocity set, geometry, walls, tau, force, chi, eps and start may
+ * differ) stepped together: each dependency level of the step (Sec. 3.2)
+ * launches the roundings and fits of that level of every simulation at once,
+ * and one CUDA graph holds the whole batched step.  The paper runs one simulation at a
+ * time; results are bitwise those of the simulations stepped alone when the
+ * rounding launches use the same cluster sizes (always in TNLBM_FP32 and
+ * TNLBM_TF32, where every job runs on one CTA). */
 typedef struct tnlbm_batch tnlbm_batch; /* opaque; owns its simulations */
 
 /* Creates cfgs[0..nsim) (1 <= nsim <= 64) as for tnlbm_create.  On error no
@@ -403,6 +442,13 @@ tnlbm_sim *tnlbm_batch_sim(tnlbm_batch *b, int i);
  * batched step; any pointer may be NULL. */
 int tnlbm_batch_info(tnlbm_batch *b, int *nsim, int *launches_per_step,
                      int *jobs_per_step);
+/* tnlbm_clusters / tnlbm_set_clusters / tnlbm_tune_clusters for the batched
+ * step, whose rounding launch of a level holds the jobs of every simulation;
+ * the cap is the smallest max_cluster of the simulations.  Tuning leaves every
+ * simulation's populations, step count and discarded weight unchanged. */
+int tnlbm_batch_clusters(tnlbm_batch *b, int *clusters, int *jobs, int cap, int *nlevels);
+int tnlbm_batch_set_clusters(tnlbm_batch *b, const int *clusters, int nlevels);
+int tnlbm_batch_tune_clusters(tnlbm_batch *b, int reps, double *ms, int ms_cap);
 int tnlbm_batch_destroy(tnlbm_batch *b);
 
 /* ------------------------------------------------------------------ learned rounding

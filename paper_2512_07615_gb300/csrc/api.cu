@@ -623,6 +623,133 @@ static int capture_graph(tnlbm_sim* s) {
   return 0;
 }
 
+// ------------------------------------------------------------ cluster tuning
+// Cluster sizes the tuner times for a rounding launch (largest first), besides
+// the size the level already has.
+static const int TUNE_P[] = {16, 8, 4, 2, 1};
+
+// Times run(P) -- one rounding launch of a level with clusters of P CTAs, on
+// stream st -- at the current size `cur` and then at the sizes of TUNE_P that
+// fit (P <= cap and resident on this device), each the minimum of `reps`
+// launches.  Below cur, smaller sizes are skipped once one is 1.5x slower
+// than the best so far: with more jobs than fit at once, large clusters run
+// in waves, while small ones spread each FP64 SVD over fewer SMs, so the time
+// falls and then rises as P shrinks.  ms[P] gets the time of size P (-1 where
+// not timed); *best the fastest, where cur stays unless another size is 2 %
+// faster.  Every launch writes the level's outputs again, from the same
+// inputs.
+template <typename T, typename F>
+static int tune_launch(F&& run, int cap, int reps, int cur, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                       double* ms, int* best) {
+  double t[TNLBM_CLUSTER_MAX + 1];
+  for (int P = 0; P <= TNLBM_CLUSTER_MAX; ++P) t[P] = -1.0;
+  std::vector<int> cand;                    // the current size first, then the others from 16 down
+  if (cur >= 1 && cur <= TNLBM_CLUSTER_MAX && round_cluster_resident<T>(cur) >= 1) cand.push_back(cur);
+  for (int P : TUNE_P)
+    if (P != cur && P <= cap && round_cluster_resident<T>(P) >= 1) cand.push_back(P);
+  int pb = -1;
+  for (int P : cand) {
+    double tm = 1e300;
+    for (int r = 0; r < std::max(reps, 1); ++r) {
+      TN_CUDA(cudaEventRecord(e0, st));
+      run(P);
+      TN_CUDA(cudaGetLastError());
+      TN_CUDA(cudaEventRecord(e1, st));
+      TN_CUDA(cudaEventSynchronize(e1));
+      float f = 0.f;
+      TN_CUDA(cudaEventElapsedTime(&f, e0, e1));
+      tm = std::min(tm, (double)f);
+    }
+    t[P] = tm;
+    if (pb < 0 || tm < t[pb]) pb = P;
+    else if (P < cur || cur < 1) {
+      if (tm > 1.5 * t[pb]) break;
+    }
+  }
+  if (pb < 0) { set_error("no cluster size of the rounding kernel fits on this device"); return TNLBM_E_CUDA; }
+  if (cur >= 1 && cur <= TNLBM_CLUSTER_MAX && t[cur] >= 0.0 && t[cur] <= 1.02 * t[pb]) pb = cur;
+  if (ms)
+    for (int P = 0; P <= TNLBM_CLUSTER_MAX; ++P) ms[P] = t[P];
+  *best = pb;
+  return 0;
+}
+
+// Whether the rounding jobs of a precision run as clusters: the CTAs of a
+// cluster share the FP64 centre SVDs, so FP32 and TF32 jobs run one CTA each.
+static bool clusters_apply(int prec) { return prec_svd64(prec) || prec == TNLBM_FP64; }
+
+// Checks a cluster size given for a level of njobs rounding jobs.
+template <typename T>
+static int check_cluster(int prec, int P) {
+  if (P < 1 || P > TNLBM_CLUSTER_MAX) { set_error("cluster sizes are 1..16"); return TNLBM_E_ARG; }
+  if (P > 1 && !clusters_apply(prec)) {
+    set_error("FP32 and TF32 rounding jobs run one CTA each (cluster size 1)");
+    return TNLBM_E_ARG;
+  }
+  if (round_cluster_resident<T>(P) < 1) {
+    set_error("clusters of " + std::to_string(P) + " CTAs of the rounding kernel do not fit on this device");
+    return TNLBM_E_ARG;
+  }
+  return 0;
+}
+
+// Runs one step of a simulation eagerly on s0, level by level, timing each
+// rounding launch at every candidate cluster size and keeping the fastest;
+// the final copy into the populations (and the mass correction before it) is
+// left out, so the state, the step count and the discarded-weight total are
+// as before.  ms: [levels][17] times (may be NULL).  Re-captures the graph.
+template <typename T>
+static int tune_sim(tnlbm_sim* s, int reps, double* ms, int ms_cap) {
+  if (s->learn_mode) { set_error("tune the cluster sizes before configuring the learned rounding"); return TNLBM_E_ARG; }
+  TN_CUDA(cudaStreamSynchronize(s->s0));
+  double disc = 0.0;
+  TN_CUDA(cudaMemcpy(&disc, s->d_discard, sizeof(double), cudaMemcpyDeviceToHost));
+  const int cap = s->cfg.max_cluster > 0 ? std::min(s->cfg.max_cluster, (int)TNLBM_CLUSTER_MAX) : TNLBM_CLUSTER_MAX;
+  const bool tune = clusters_apply(s->prec) && cap > 1;
+  std::vector<int> old;
+  for (auto& lv : s->levels) old.push_back(lv.cluster);
+  std::vector<double> t((size_t)s->levels.size() * (TNLBM_CLUSTER_MAX + 1), -1.0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TN_CUDA(cudaEventCreate(&e0));
+  TN_CUDA(cudaEventCreate(&e1));
+  int rc = 0;
+  for (size_t l = 0; l < s->levels.size() && !rc; ++l) {
+    auto& lv = s->levels[l];
+    if (lv.has_rho0) launch_rho0<T>(s->d_rho_ref, s->L, s->n_fluid, s->d_scal, s->s0);
+    if (!lv.fj.empty())
+      run_fit<T>(lv.d_fj, lv.fj, s->L, s->cfg.sweeps, s->d_status, s->s0, nullptr, prec_tc(s->prec));
+    if (!lv.zj.empty()) run_zipup<T>(lv.d_zj, (int)lv.zj.size(), s->L, s->d_status, s->s0, nullptr);
+    if (lv.rj.empty()) continue;
+    auto run = [&](int P) {
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), s->L, s->n, (const T*)s->d_masks, s->d_scal, s->d_status,
+                      s->s0, nullptr, nullptr, P);
+    };
+    if (tune) {
+      int best = lv.cluster;
+      rc = tune_launch<T>(run, cap, reps, lv.cluster, s->s0, e0, e1, t.data() + l * (TNLBM_CLUSTER_MAX + 1), &best);
+      if (!rc) lv.cluster = best;
+    } else {
+      run(lv.cluster);
+    }
+  }
+  cudaStreamSynchronize(s->s0);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TN_CUDA(cudaMemcpy(s->d_discard, &disc, sizeof(double), cudaMemcpyHostToDevice));
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, s->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (!rc && st[0]) {
+    rc = status_to_code(st);
+    TN_CUDA(cudaMemset(s->d_status, 0, STATUS_INTS * sizeof(int)));
+  }
+  if (rc)
+    for (size_t l = 0; l < s->levels.size(); ++l) s->levels[l].cluster = old[l];
+  else if (ms)
+    std::copy(t.begin(), t.begin() + std::min<size_t>(t.size(), std::max(ms_cap, 0)), ms);
+  const int rc2 = capture_graph<T>(s);
+  return rc ? rc : rc2;
+}
+
 // Switch the learned rounding of a simulation (see tnlbm_learn_configure).
 template <typename T>
 static int learn_configure_impl(tnlbm_sim* s, int mode, const double* omega, int rows, int ld,
@@ -1030,6 +1157,60 @@ int tnlbm_step(tnlbm_sim* s, int k) {
     return rc;
   }
   return 0;
+}
+
+}  // extern "C"
+
+namespace tn {
+
+template <typename LV>
+static int get_clusters(const std::vector<LV>& levels, int* clusters, int* jobs, int cap, int* nlevels) {
+  const int n = (int)levels.size();
+  for (int l = 0; l < std::min(std::max(cap, 0), n); ++l) {
+    if (clusters) clusters[l] = levels[l].rj.empty() ? 0 : levels[l].cluster;
+    if (jobs) jobs[l] = (int)levels[l].rj.size();
+  }
+  if (nlevels) *nlevels = n;
+  return 0;
+}
+
+template <typename T, typename LV>
+static int set_clusters(std::vector<LV>& levels, int prec, const int* clusters, int nlevels) {
+  if (!clusters || nlevels != (int)levels.size()) {
+    set_error("setting cluster sizes needs one entry per dependency level (" + std::to_string(levels.size()) + ")");
+    return TNLBM_E_ARG;
+  }
+  for (int l = 0; l < nlevels; ++l)
+    if (!levels[l].rj.empty()) {
+      const int rc = check_cluster<T>(prec, clusters[l]);
+      if (rc) return rc;
+    }
+  for (int l = 0; l < nlevels; ++l)
+    if (!levels[l].rj.empty()) levels[l].cluster = clusters[l];
+  return 0;
+}
+
+}  // namespace tn
+
+extern "C" {
+
+int tnlbm_clusters(tnlbm_sim* s, int* clusters, int* jobs, int cap, int* nlevels) {
+  if (!s) { set_error("bad arguments to tnlbm_clusters"); return TNLBM_E_ARG; }
+  return tn::get_clusters(s->levels, clusters, jobs, cap, nlevels);
+}
+
+int tnlbm_set_clusters(tnlbm_sim* s, const int* clusters, int nlevels) {
+  if (!s) { set_error("bad arguments to tnlbm_set_clusters"); return TNLBM_E_ARG; }
+  const bool f64 = s->prec == TNLBM_FP64;
+  int rc = f64 ? tn::set_clusters<double>(s->levels, s->prec, clusters, nlevels)
+               : tn::set_clusters<float>(s->levels, s->prec, clusters, nlevels);
+  if (rc) return rc;
+  return f64 ? tn::capture_graph<double>(s) : tn::capture_graph<float>(s);
+}
+
+int tnlbm_tune_clusters(tnlbm_sim* s, int reps, double* ms, int ms_cap) {
+  if (!s || reps < 1 || (ms && ms_cap < 0)) { set_error("bad arguments to tnlbm_tune_clusters"); return TNLBM_E_ARG; }
+  return s->prec == TNLBM_FP64 ? tn::tune_sim<double>(s, reps, ms, ms_cap) : tn::tune_sim<float>(s, reps, ms, ms_cap);
 }
 
 }  // extern "C"
@@ -1772,6 +1953,7 @@ struct tnlbm_batch {
   };
   std::vector<CopyGroup> copies;   // indexed like lens
   int launches_per_step = 0;
+  int cap = 16;                    // largest cluster size (smallest max_cluster of the simulations)
 };
 
 namespace tn {
@@ -1827,12 +2009,92 @@ static int enqueue_batch_step(tnlbm_batch* b, int* launches) {
   return 0;
 }
 
+// (re)capture one batched step as a graph
+template <typename T>
+static int batch_capture(tnlbm_batch* b) {
+  TN_CUDA(cudaStreamSynchronize(b->s0));
+  if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  TN_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+  int launches = 0;
+  enqueue_batch_step<T>(b, &launches);
+  TN_CUDA(cudaStreamEndCapture(b->s0, &b->graph));
+  TN_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  b->launches_per_step = launches;
+  return 0;
+}
+
+// tune_sim for a batch: one eager batched step on s0 without the final
+// copies, each level's rounding launch timed at the candidate cluster sizes.
+template <typename T>
+static int tune_batch(tnlbm_batch* b, int reps, double* ms, int ms_cap) {
+  for (tnlbm_sim* s : b->sims)
+    if (s->learn_mode) { set_error("tune the cluster sizes before configuring the learned rounding"); return TNLBM_E_ARG; }
+  TN_CUDA(cudaStreamSynchronize(b->s0));
+  const int ns = (int)b->sims.size();
+  std::vector<double> disc(ns, 0.0);
+  for (int i = 0; i < ns; ++i)
+    TN_CUDA(cudaMemcpy(&disc[i], b->sims[i]->d_discard, sizeof(double), cudaMemcpyDeviceToHost));
+  const bool tune = clusters_apply(b->prec) && b->cap > 1;
+  std::vector<int> old;
+  for (auto& lv : b->levels) old.push_back(lv.cluster);
+  std::vector<double> t((size_t)b->levels.size() * (TNLBM_CLUSTER_MAX + 1), -1.0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TN_CUDA(cudaEventCreate(&e0));
+  TN_CUDA(cudaEventCreate(&e1));
+  int rc = 0;
+  for (size_t l = 0; l < b->levels.size() && !rc; ++l) {
+    auto& lv = b->levels[l];
+    for (int si : lv.rho0) {
+      tnlbm_sim* s = b->sims[si];
+      launch_rho0<T>(s->d_rho_ref, s->L, s->n_fluid, s->d_scal, b->s0);
+    }
+    for (size_t gi = 0; gi < b->lens.size(); ++gi) {
+      auto& g = lv.fg[gi];
+      if (!g.fj.empty())
+        run_fit<T>(g.d_fj, g.fj, b->lens[gi], b->sweeps, b->d_status, b->s0, nullptr, prec_tc(b->prec));
+      if (!g.zj.empty()) run_zipup<T>(g.d_zj, (int)g.zj.size(), b->lens[gi], b->d_status, b->s0, nullptr);
+    }
+    if (lv.rj.empty()) continue;
+    auto run = [&](int P) {
+      launch_round<T>(lv.d_rj, (int)lv.rj.size(), b->lens.back(), 0, nullptr, nullptr, b->d_status, b->s0,
+                      nullptr, nullptr, P);
+    };
+    if (tune) {
+      int best = lv.cluster;
+      rc = tune_launch<T>(run, b->cap, reps, lv.cluster, b->s0, e0, e1,
+                          t.data() + l * (TNLBM_CLUSTER_MAX + 1), &best);
+      if (!rc) lv.cluster = best;
+    } else {
+      run(lv.cluster);
+    }
+  }
+  cudaStreamSynchronize(b->s0);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int i = 0; i < ns; ++i)
+    TN_CUDA(cudaMemcpy(b->sims[i]->d_discard, &disc[i], sizeof(double), cudaMemcpyHostToDevice));
+  int st[STATUS_INTS] = {0};
+  TN_CUDA(cudaMemcpy(st, b->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+  if (!rc && st[0]) {
+    rc = status_to_code(st);
+    TN_CUDA(cudaMemset(b->d_status, 0, STATUS_INTS * sizeof(int)));
+  }
+  if (rc)
+    for (size_t l = 0; l < b->levels.size(); ++l) b->levels[l].cluster = old[l];
+  else if (ms)
+    std::copy(t.begin(), t.begin() + std::min<size_t>(t.size(), std::max(ms_cap, 0)), ms);
+  const int rc2 = batch_capture<T>(b);
+  return rc ? rc : rc2;
+}
+
 template <typename T>
 static int batch_build(tnlbm_batch* b) {
   for (tnlbm_sim* s : b->sims) b->lens.push_back(s->L);
   std::sort(b->lens.begin(), b->lens.end());
   b->lens.erase(std::unique(b->lens.begin(), b->lens.end()), b->lens.end());
   const int ng = (int)b->lens.size();
+  for (tnlbm_sim* s : b->sims) b->cap = std::min(b->cap, s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16);
   auto group = [&](int L) { return (int)(std::lower_bound(b->lens.begin(), b->lens.end(), L) - b->lens.begin()); };
   TN_CUDA(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
   TN_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
@@ -1878,10 +2140,7 @@ static int batch_build(tnlbm_batch* b) {
       lv.d_rj = (RoundJob*)b->arena.alloc(lv.rj.size() * sizeof(RoundJob));
       if (!lv.d_rj) return TNLBM_E_OOM;
       TN_CUDA(cudaMemcpy(lv.d_rj, lv.rj.data(), lv.rj.size() * sizeof(RoundJob), cudaMemcpyHostToDevice));
-      int cap = 16;
-      for (tnlbm_sim* s : b->sims) cap = std::min(cap, s->cfg.max_cluster > 0 ? s->cfg.max_cluster : 16);
-      lv.cluster = (prec_svd64(b->prec) || b->prec == TNLBM_FP64) && cap > 1
-                       ? round_cluster_size<T>((int)lv.rj.size(), cap) : 1;
+      lv.cluster = clusters_apply(b->prec) && b->cap > 1 ? round_cluster_size<T>((int)lv.rj.size(), b->cap) : 1;
     }
     for (auto& g : lv.fg) {
       if (g.fj.empty()) continue;
@@ -1907,13 +2166,7 @@ static int batch_build(tnlbm_batch* b) {
     TN_CUDA(cudaMemcpy(c.d_dst, dst[gi].data(), c.n * sizeof(MpsRef), cudaMemcpyHostToDevice));
   }
   TN_CUDA(cudaDeviceSynchronize());
-  TN_CUDA(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
-  int launches = 0;
-  enqueue_batch_step<T>(b, &launches);
-  TN_CUDA(cudaStreamEndCapture(b->s0, &b->graph));
-  TN_CUDA(cudaGraphInstantiate(&b->gexec, b->graph, 0));
-  b->launches_per_step = launches;
-  return 0;
+  return batch_capture<T>(b);
 }
 
 static int batch_status(tnlbm_batch* b) {
@@ -2025,6 +2278,25 @@ int tnlbm_batch_info(tnlbm_batch* b, int* nsim, int* launches_per_step, int* job
     *jobs_per_step = j;
   }
   return 0;
+}
+
+int tnlbm_batch_clusters(tnlbm_batch* b, int* clusters, int* jobs, int cap, int* nlevels) {
+  if (!b) { set_error("bad arguments to tnlbm_batch_clusters"); return TNLBM_E_ARG; }
+  return tn::get_clusters(b->levels, clusters, jobs, cap, nlevels);
+}
+
+int tnlbm_batch_set_clusters(tnlbm_batch* b, const int* clusters, int nlevels) {
+  if (!b) { set_error("bad arguments to tnlbm_batch_set_clusters"); return TNLBM_E_ARG; }
+  const bool f64 = b->prec == TNLBM_FP64;
+  int rc = f64 ? tn::set_clusters<double>(b->levels, b->prec, clusters, nlevels)
+               : tn::set_clusters<float>(b->levels, b->prec, clusters, nlevels);
+  if (rc) return rc;
+  return f64 ? tn::batch_capture<double>(b) : tn::batch_capture<float>(b);
+}
+
+int tnlbm_batch_tune_clusters(tnlbm_batch* b, int reps, double* ms, int ms_cap) {
+  if (!b || reps < 1 || (ms && ms_cap < 0)) { set_error("bad arguments to tnlbm_batch_tune_clusters"); return TNLBM_E_ARG; }
+  return b->prec == TNLBM_FP64 ? tn::tune_batch<double>(b, reps, ms, ms_cap) : tn::tune_batch<float>(b, reps, ms, ms_cap);
 }
 
 }  // extern "C"

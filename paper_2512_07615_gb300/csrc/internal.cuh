@@ -222,6 +222,10 @@ size_t round_smem_bytes();
 // are resident at once on the current device; 1 if none.
 template <typename T>
 int round_cluster_size(int njobs, int cap);
+// how many clusters of P CTAs of the rounding kernel are resident at once on
+// the current device (0: that size cannot launch)
+template <typename T>
+int round_cluster_resident(int P);
 // increments the device step counter read by the rank model
 void launch_learn_tick(int* d_step, cudaStream_t st);
 

@@ -1641,39 +1641,46 @@ void launch_round(const RoundJob* d_jobs, int njobs, int L, int n_bits, const T*
   cudaLaunchKernelEx(&cfg, round_kernel<T>, d_jobs, L, n_bits, d_masks, d_scal, d_status, d_ctr, d_learn);
 }
 
+// Resident clusters of P CTAs (1 <= P <= 16) of the rounding kernel on the
+// current device; the table is queried once per device.
 template <typename T>
-int round_cluster_size(int njobs, int cap) {
-  // resident clusters of each size 1..16 on this device (queried once per device)
+int round_cluster_resident(int P) {
   static int cached_dev = -1;
   static int max_active[CL_MAX + 1];
+  if (P < 1 || P > CL_MAX) return 0;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (dev != cached_dev) {
     cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)round_smem_bytes());
     cudaFuncSetAttribute(round_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    for (int P = 1; P <= CL_MAX; ++P) {
+    for (int q = 1; q <= CL_MAX; ++q) {
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(P, 1, 1);
+      cfg.gridDim = dim3(q, 1, 1);
       cfg.blockDim = dim3(RT, 1, 1);
       cfg.dynamicSmemBytes = round_smem_bytes();
       cudaLaunchAttribute at[1];
       at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = P;
+      at[0].val.clusterDim.x = q;
       at[0].val.clusterDim.y = 1;
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int n = 0;
       if (cudaOccupancyMaxActiveClusters(&n, round_kernel<T>, &cfg) != cudaSuccess) n = 0;
-      max_active[P] = n;
+      max_active[q] = n;
     }
     cudaGetLastError();
     cached_dev = dev;
   }
+  return max_active[P];
+}
+
+template <typename T>
+int round_cluster_size(int njobs, int cap) {
   // the largest cluster at which every job of the launch is resident at once
   // (the FP64 Jacobi scales with the SMs of its cluster)
   for (int P = imin(cap, CL_MAX); P >= 2; --P)
-    if (max_active[P] >= njobs) return P;
+    if (round_cluster_resident<T>(P) >= njobs) return P;
   return 1;
 }
 
@@ -1683,5 +1690,7 @@ template void launch_round<double>(const RoundJob*, int, int, int, const double*
                                    const double*, int*, cudaStream_t, double*, const LearnCtx*, int);
 template int round_cluster_size<float>(int, int);
 template int round_cluster_size<double>(int, int);
+template int round_cluster_resident<float>(int);
+template int round_cluster_resident<double>(int);
 
 }  // namespace tn

@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "libtnlbm.so")
 
 FP64, FP32, TF32, MIXED, BF16 = 0, 1, 2, 3, 4
 D3Q19, D3Q15 = 19, 15
+CLUSTER_MAX = 16   # TNLBM_CLUSTER_MAX
 FACE_WALL, FACE_VELOCITY, FACE_PRESSURE = 0, 1, 2
 HADAMARD_FIT, HADAMARD_EXACT, HADAMARD_ZIPUP = 0, 1, 2
 TERM_PLAIN, TERM_SHIFT, TERM_MASK1, TERM_KRON, TERM_ONES = 0, 1, 2, 3, 4
@@ -146,6 +147,12 @@ SIGNATURES = {
     "tnlbm_batch_sim": (ctypes.c_void_p, [ctypes.c_void_p, ctypes.c_int]),
     "tnlbm_batch_info": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, c_int_p]),
     "tnlbm_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "tnlbm_clusters": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, ctypes.c_int, c_int_p]),
+    "tnlbm_set_clusters": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int]),
+    "tnlbm_tune_clusters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_int]),
+    "tnlbm_batch_clusters": (ctypes.c_int, [ctypes.c_void_p, c_int_p, c_int_p, ctypes.c_int, c_int_p]),
+    "tnlbm_batch_set_clusters": (ctypes.c_int, [ctypes.c_void_p, c_int_p, ctypes.c_int]),
+    "tnlbm_batch_tune_clusters": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_int]),
     "tnlbm_mask_product": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),

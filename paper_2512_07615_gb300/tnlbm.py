@@ -2,6 +2,8 @@
 flat layout of include/tnlbm.h), the simulation handle, and the batched
 primitives.  No arithmetic of the method happens here."""
 import ctypes
+import json
+import os
 
 import numpy as np
 import torch
@@ -373,7 +375,84 @@ def make_config(n_per_axis, lattice=nat.D3Q19, tau=0.8, periodic=(1, 1, 1), soli
     return c, keep
 
 
-class Sim:
+def cluster_cache_key(device, configs, jobs):
+    """Key of a cluster-size choice in a JSON cache: the device name, each
+    simulation's (n_per_axis, lattice, chi_max, precision, max_cluster, fit
+    sweeps) and the rounding jobs of every dependency level."""
+    sims = [[int(c.n_per_axis), int(c.lattice), int(c.chi_max), int(c.precision), int(c.max_cluster),
+             int(c.sweeps)] for c in configs]
+    return json.dumps({"device": str(device), "sims": sims, "jobs": [int(j) for j in jobs]}, sort_keys=True)
+
+
+def load_cluster_cache(path):
+    """The {key: sizes} table stored at path ({} if there is none)."""
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return d if isinstance(d, dict) else {}
+
+
+def store_cluster_cache(path, key, sizes):
+    """Adds key -> sizes to the table at path (written to a temporary file
+    and renamed, so a reader never sees half a file)."""
+    d = load_cluster_cache(path)
+    d[key] = [int(x) for x in sizes]
+    tmp = "%s.%d.tmp" % (path, os.getpid())
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+class _Clusters:
+    """Per-level cluster sizes of the rounding launches of a simulation or a
+    batch (tnlbm_clusters / tnlbm_set_clusters / tnlbm_tune_clusters)."""
+    _fn = ("tnlbm_clusters", "tnlbm_set_clusters", "tnlbm_tune_clusters")
+
+    def clusters(self):
+        """(sizes, jobs): per dependency level, the CTAs per rounding job (0
+        where the level has no rounding) and the level's rounding jobs."""
+        get = getattr(nat.lib(), self._fn[0])
+        n = ctypes.c_int()
+        nat.check(get(self.h, None, None, 0, ctypes.byref(n)), self._fn[0])
+        c = (ctypes.c_int * max(n.value, 1))()
+        j = (ctypes.c_int * max(n.value, 1))()
+        nat.check(get(self.h, c, j, n.value, ctypes.byref(n)), self._fn[0])
+        return list(c)[:n.value], list(j)[:n.value]
+
+    def set_clusters(self, sizes):
+        """Sets every level's cluster size (one entry per level) and
+        re-captures the step's graph."""
+        arr = (ctypes.c_int * max(len(sizes), 1))(*[int(x) for x in sizes])
+        nat.check(getattr(nat.lib(), self._fn[1])(self.h, arr, len(sizes)), self._fn[1])
+
+    def tune_clusters(self, reps=2, cache=None):
+        """Times each level's rounding launch at the candidate cluster sizes
+        and keeps the fastest; the populations and the step count are left as
+        they were.  cache: a JSON file; a choice stored there for this device
+        and level structure is applied without timing, a new one is stored.
+        Returns dict(sizes, jobs, ms: per level {P: ms} or None, cached)."""
+        sizes, jobs = self.clusters()
+        key = None
+        if cache is not None:
+            key = cluster_cache_key(torch.cuda.get_device_name(), self._configs(), jobs)
+            hit = load_cluster_cache(cache).get(key)
+            if hit is not None and len(hit) == len(sizes):
+                self.set_clusters(hit)
+                return dict(sizes=list(hit), jobs=jobs, ms=None, cached=True)
+        stride = nat.CLUSTER_MAX + 1
+        buf = (ctypes.c_double * max(len(sizes) * stride, 1))()
+        nat.check(getattr(nat.lib(), self._fn[2])(self.h, int(reps), buf, len(buf)), self._fn[2])
+        ms = [{P: buf[l * stride + P] for P in range(1, stride) if buf[l * stride + P] >= 0}
+              for l in range(len(sizes))]
+        sizes, _ = self.clusters()
+        if key is not None:
+            store_cluster_cache(cache, key, sizes)
+        return dict(sizes=sizes, jobs=jobs, ms=ms, cached=False)
+
+
+class Sim(_Clusters):
     """Handle of a tnlbm_sim (tnlbm_create ... tnlbm_destroy)."""
 
     def __init__(self, n_per_axis, **kw):
@@ -384,6 +463,9 @@ class Sim:
         self.h = h
         self._owned = True
         del keep
+
+    def _configs(self):
+        return [self.cfg]
 
     def _init_fields(self, c):
         self.cfg = c
@@ -531,10 +613,14 @@ class Sim:
             pass
 
 
-class Batch:
-    """Several simulations of the same lattice size stepped together
+class Batch(_Clusters):
+    """Several simulations (lattice sizes may differ) stepped together
     (tnlbm_batch_create ... tnlbm_batch_destroy).  configs: list of keyword
     dicts for make_config (each with n_per_axis)."""
+    _fn = ("tnlbm_batch_clusters", "tnlbm_batch_set_clusters", "tnlbm_batch_tune_clusters")
+
+    def _configs(self):
+        return [s.cfg for s in self.sims]
 
     def __init__(self, configs):
         made = [make_config(**kw) for kw in configs]
