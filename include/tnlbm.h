@@ -255,9 +255,10 @@ int tnlbm_set_clusters(tnlbm_sim *s, const int *clusters, int nlevels);
 
 /* Measures the cluster size of every level.  Runs one step eagerly, level by
  * level, and times each rounding launch (CUDA events; the minimum of reps >= 1
- * launches) at P = 16, 8, 4, 2, 1 and at the level's current size, among the
- * sizes <= tnlbm_config.max_cluster that fit on the device, going down until
- * a size is 1.5x slower than the best so far.  Each level keeps its fastest
+ * launches) at the level's current size, at P = 16, 8, 4, 2, 1 (going down
+ * until a size is 1.5x slower than the best so far), then at 3/4 and 3/2 of
+ * the fastest, among the sizes <= tnlbm_config.max_cluster that fit on the
+ * device.  Each level keeps its fastest
  * size (the current one unless another is 2 % faster); the graph is then
  * re-captured.  The step's copy into the populations (and the mass correction
  * before it) is left out: the populations, the step count and the total

@@ -629,11 +629,12 @@ static int capture_graph(tnlbm_sim* s) {
 static const int TUNE_P[] = {16, 8, 4, 2, 1};
 
 // Times run(P) -- one rounding launch of a level with clusters of P CTAs, on
-// stream st -- at the current size `cur` and then at the sizes of TUNE_P that
-// fit (P <= cap and resident on this device), each the minimum of `reps`
-// launches.  Below cur, smaller sizes are skipped once one is 1.5x slower
-// than the best so far: with more jobs than fit at once, large clusters run
-// in waves, while small ones spread each FP64 SVD over fewer SMs, so the time
+// stream st -- at the current size `cur`, then at the sizes of TUNE_P, then
+// at 3/4 and 3/2 of the fastest of those, among the sizes that fit (P <= cap
+// and resident on this device); each time is the minimum of `reps` launches.
+// Below cur, smaller sizes of TUNE_P are skipped once one is 1.5x slower than
+// the best so far: with more jobs than fit at once, large clusters run in
+// waves, while small ones spread each FP64 SVD over fewer SMs, so the time
 // falls and then rises as P shrinks.  ms[P] gets the time of size P (-1 where
 // not timed); *best the fastest, where cur stays unless another size is 2 %
 // faster.  Every launch writes the level's outputs again, from the same
@@ -647,8 +648,7 @@ static int tune_launch(F&& run, int cap, int reps, int cur, cudaStream_t st, cud
   if (cur >= 1 && cur <= TNLBM_CLUSTER_MAX && round_cluster_resident<T>(cur) >= 1) cand.push_back(cur);
   for (int P : TUNE_P)
     if (P != cur && P <= cap && round_cluster_resident<T>(P) >= 1) cand.push_back(P);
-  int pb = -1;
-  for (int P : cand) {
+  auto time_at = [&](int P, double* out) -> int {
     double tm = 1e300;
     for (int r = 0; r < std::max(reps, 1); ++r) {
       TN_CUDA(cudaEventRecord(e0, st));
@@ -660,13 +660,30 @@ static int tune_launch(F&& run, int cap, int reps, int cur, cudaStream_t st, cud
       TN_CUDA(cudaEventElapsedTime(&f, e0, e1));
       tm = std::min(tm, (double)f);
     }
-    t[P] = tm;
-    if (pb < 0 || tm < t[pb]) pb = P;
+    *out = tm;
+    return 0;
+  };
+  int pb = -1;
+  for (int P : cand) {
+    const int rc = time_at(P, &t[P]);
+    if (rc) return rc;
+    if (pb < 0 || t[P] < t[pb]) pb = P;
     else if (P < cur || cur < 1) {
-      if (tm > 1.5 * t[pb]) break;
+      if (t[P] > 1.5 * t[pb]) break;
     }
   }
   if (pb < 0) { set_error("no cluster size of the rounding kernel fits on this device"); return TNLBM_E_CUDA; }
+  // then the sizes halfway to the best one's neighbours (3 and 6 around 4,
+  // 6 and 12 around 8, ...): the number of waves moves in steps of whole
+  // waves, so the optimum need not be a power of two
+  const int best2 = pb;
+  for (int P : {best2 * 3 / 4, best2 * 3 / 2}) {
+    if (P < 1 || P > cap || P > TNLBM_CLUSTER_MAX || t[P] >= 0.0) continue;
+    if (round_cluster_resident<T>(P) < 1) continue;
+    const int rc = time_at(P, &t[P]);
+    if (rc) return rc;
+    if (t[P] < t[pb]) pb = P;
+  }
   if (cur >= 1 && cur <= TNLBM_CLUSTER_MAX && t[cur] >= 0.0 && t[cur] <= 1.02 * t[pb]) pb = cur;
   if (ms)
     for (int P = 0; P <= TNLBM_CLUSTER_MAX; ++P) ms[P] = t[P];
