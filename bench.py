@@ -346,11 +346,12 @@ MIXED_SIZES = (6, 7, 8, 6, 7, 6, 8, 7)
 MIXED_CHIS = (32, 64, 128)
 
 
-def mixed_batch_configs():
+def mixed_batch_configs(precision=1):
     """Eight simulations of uneven size: 64^3 / 128^3 / 256^3 in the order of
     MIXED_SIZES, chi cycling 32 / 64 / 128; even seeds are sphere packs (radius
     10 cells per 128, 35 % solid), odd seeds branching vessels (root radius 24
-    cells per 256, depth 4); FP32, eps 1e-7, seeded smooth starts."""
+    cells per 256, depth 4); eps 1e-7, seeded smooth starts; FP32 unless
+    another precision is given."""
     import synth
     out = []
     for i, n in enumerate(MIXED_SIZES):
@@ -359,19 +360,26 @@ def mixed_batch_configs():
         solid = synth.sphere_pack(n, 10.0 * N / 128, 0.35, i) if i % 2 == 0 else \
             synth.vessel_tree(n, 24.0 * N / 256, 4, i)
         out.append(dict(n_per_axis=n, tau=0.7, periodic=(1, 1, 1), solid=solid, chi_mask=chi, eps_mask=1e-8,
-                        force=(1e-5, 0, 0), chi_max=chi, eps=1e-7, precision=1, hadamard=0, sweeps=2,
+                        force=(1e-5, 0, 0), chi_max=chi, eps=1e-7, precision=precision, hadamard=0, sweeps=2,
                         modes=synth.fourier_modes(31, i, kmax=4, amp_rho=1e-3, amp_u=1e-3), conserve_mass=True))
     return out
 
 
-def mixed_batch_measurement(warmup=1, steps=2):
-    """The uneven batch stepped in one graph against the same simulations
+def mixed_batch_measurement(precision=1, warmup=1, steps=2, tune=True):
+    """The uneven batch stepped in one graph (cluster sizes tuned per level
+    first where the precision runs clusters) against the same simulations
     stepped one after another (one step each, after one untimed step)."""
     import paper_2512_07615_gb300 as tl
-    cfgs = mixed_batch_configs()
+    cfgs = mixed_batch_configs(precision)
     cells = sum((1 << c["n_per_axis"]) ** 3 for c in cfgs)
     b = tl.Batch(cfgs)
     info = b.info()
+    tuned = None
+    if tune and precision in (0, 3, 4):
+        b.step(1)                       # bonds at their working size before the sizes are measured
+        t = time.perf_counter()
+        r = b.tune_clusters(reps=1)
+        tuned = {"tune_s": round(time.perf_counter() - t, 2), "sizes": r["sizes"], "jobs_per_level": r["jobs"]}
     b.step(warmup)
     ms = b.step_timed(steps) / steps
     bonds = [s.stats()["max_bond"] for s in b.sims]
@@ -385,7 +393,9 @@ def mixed_batch_measurement(warmup=1, steps=2):
         alone.append(s.step_timed(1))
         s.close()
     return {"workload": "mixed8: sizes %s^3, chi %s cycling, sphere packs (even seeds) and vessels (odd seeds), "
-                        "FP32" % ("/".join(str(1 << n) for n in MIXED_SIZES), "/".join(map(str, MIXED_CHIS))),
+                        "%s" % ("/".join(str(1 << n) for n in MIXED_SIZES), "/".join(map(str, MIXED_CHIS)),
+                                PREC_NAME[precision]),
+            "cluster_tuning": tuned,
             "value": cells / (ms * 1e3), "unit": "MLUPS", "ms_per_step": ms, "steps": steps, "warmup": warmup,
             "launches_per_step": info["launches_per_step"], "jobs_per_step": info["jobs_per_step"],
             "max_bonds": bonds, "unbatched_ms_per_round": sum(alone), "unbatched_ms_each": alone,
@@ -471,6 +481,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-precision", choices=sorted(PREC), default="mixed",
                     help="precision of the batched eight-simulation leg")
+    ap.add_argument("--uneven-precision", choices=sorted(PREC), default="fp32",
+                    help="precision of the uneven batch (--batched-mixed)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the occupancy rule's cluster sizes (no per-level tuning)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison (vs_baseline, rel_l2_u)")
@@ -566,17 +578,19 @@ def main():
     t0 = time.time()
     sim = make_sim(w, solid, modes)
     setup_s = time.time() - t0
+    rho_start, _ = sim.macroscopic()
+    mass_start = float(rho_start.sum())
+    sim.step(args.warmup)
     tuning = None
     if not args.no_tune and w["precision"] in (0, 3, 4):
-        # per-level cluster sizes measured once before the timed steps (one
-        # eager step without its final copy: the state is unchanged)
+        # per-level cluster sizes measured once, after the warm-up steps and
+        # before the timed ones (one eager step without its final copy: the
+        # state is unchanged), then one more untimed step of the new graph
         sizes0, _ = sim.clusters()
         t0 = time.time()
         r = sim.tune_clusters(reps=1)
         tuning = {"tune_s": round(time.time() - t0, 2), "sizes": r["sizes"], "occupancy_sizes": sizes0}
-    rho_start, _ = sim.macroscopic()
-    mass_start = float(rho_start.sum())
-    sim.step(args.warmup)
+        sim.step(1)
     barrier()
     with Clocks(local) as clk:
         ms = sim.step_timed(args.steps)
@@ -681,7 +695,7 @@ def main():
         batched = batched_measurement(PREC[args.batched_precision], tune=not args.no_tune)
     batched_mixed = None
     if rank == 0 and args.batched_mixed:
-        batched_mixed = mixed_batch_measurement()
+        batched_mixed = mixed_batch_measurement(PREC[args.uneven_precision], tune=not args.no_tune)
 
     if rank == 0:
         out = {"metric": "represented MLUPS at fixed chi", "value": value, "unit": "MLUPS",
@@ -706,7 +720,7 @@ def main():
                "rounding_launch": {"jobs_per_step": st["round_jobs_per_step"], "ctas_per_step": st["round_ctas_per_step"],
                                    "max_cluster": st["max_cluster"], "cluster_tuning": tuning},
                "compression_ratio": st["compression_ratio"], "setup_s": round(setup_s, 2),
-               "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps,
+               "mass_drift": mass_drift, "mass_drift_steps": args.warmup + args.steps + (1 if tuning else 0),
                "clocks": clocks, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
                "batched": batched, "batched_mixed": batched_mixed}
         print(json.dumps(out))

@@ -128,3 +128,16 @@ def test_batch_tuning_and_members_alone_with_the_same_sizes(tl, tmp_path):
         print("member %d: max |du| = %.3e" % (i, float(np.abs(u - got[i][1]).max())))
         assert np.array_equal(rho, got[i][0]) and np.array_equal(u, got[i][1]), i
     b.close()
+
+
+def test_tuning_keeps_to_max_cluster(tl):
+    """tnlbm_config.max_cluster caps every size the tuner times and keeps
+    (BF16 mode: its centre SVDs are the mixed mode's FP64 cluster SVDs)."""
+    sim = tl.Sim(4, max_cluster=4, **porous16(4))
+    sim.step(1)
+    res = sim.tune_clusters(reps=1)
+    assert all(P <= 4 for P in res["sizes"]) and any(P > 0 for P in res["sizes"])
+    assert all(max(t) <= 4 for t in res["ms"] if t)
+    sim.step(1)
+    assert sim.stats()["status"] == 0 and sim.stats()["max_cluster"] <= 4
+    sim.close()
