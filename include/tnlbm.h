@@ -155,9 +155,10 @@ typedef struct {
                               (0 = 5 s); running out makes tnlbm_step return
                               TNLBM_E_TIMEOUT (the simulation can be destroyed) */
   int max_cluster;         /* CTAs per rounding job for the FP64 centre SVDs
-                              (TNLBM_MIXED and TNLBM_FP64): 0 = automatic (the
-                              largest size <= 16 at which every job of a
-                              dependency level is resident at once), 1 = one
+                              (TNLBM_FP64, TNLBM_MIXED, TNLBM_BF16): 0 =
+                              automatic (the largest size <= 16 at which every
+                              job of a dependency level is resident at once;
+                              tnlbm_tune_clusters measures it instead), 1 = one
                               CTA per job, else a cap (<= 16)                   */
 } tnlbm_config;
 
