@@ -429,8 +429,9 @@ int tnlbm_mask_product(int precision, int n_outer, const void *outer_dense,
  * TNLBM_TF32, where every job runs on one CTA). */
 typedef struct tnlbm_batch tnlbm_batch; /* opaque; owns its simulations */
 
-/* Creates cfgs[0..nsim) (1 <= nsim <= 64) as for tnlbm_create.  On error no
- * simulation is left allocated. */
+/* Creates cfgs[0..nsim) (1 <= nsim <= 64) as for tnlbm_create.  Batched steps
+ * round with the full truncated SVD: every learned_rank must be 0
+ * (TNLBM_E_ARG otherwise).  On error no simulation is left allocated. */
 int tnlbm_batch_create(const tnlbm_config *cfgs, int nsim, tnlbm_batch **out);
 /* k batched steps; synchronous; device status checked after the last. */
 int tnlbm_batch_step(tnlbm_batch *b, int k);

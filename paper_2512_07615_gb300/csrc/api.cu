@@ -2225,6 +2225,13 @@ int tnlbm_batch_create(const tnlbm_config* cfgs, int nsim, tnlbm_batch** out) {
       set_error("batched simulations need the same precision and fit sweeps");
       return TNLBM_E_ARG;
     }
+  // the batched rounding launches carry no learned-rounding context: a
+  // simulation with the learned rounding is stepped alone
+  for (int i = 0; i < nsim; ++i)
+    if (cfgs[i].learned_rank != 0) {
+      set_error("batched simulations take the full SVD: learned_rank must be 0 (step such a simulation alone)");
+      return TNLBM_E_ARG;
+    }
   tnlbm_batch* b = new (std::nothrow) tnlbm_batch();
   if (!b) { set_error("host allocation failed"); return TNLBM_E_OOM; }
   for (int i = 0; i < nsim; ++i) {

@@ -93,6 +93,16 @@ def test_argument_errors_of_the_newer_entry_points(lib):
     # batches
     assert lib.tnlbm_batch_create(None, 0, ctypes.byref(h)) == -1
     assert lib.tnlbm_batch_step(None, 1) == -1
+    # cluster sizes of no simulation / batch
+    n = ctypes.c_int()
+    ms = (ctypes.c_double * 17)()
+    assert lib.tnlbm_clusters(None, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.tnlbm_set_clusters(None, None, 0) == -1
+    assert lib.tnlbm_tune_clusters(None, 1, ms, 17) == -1
+    assert lib.tnlbm_batch_clusters(None, None, None, 0, ctypes.byref(n)) == -1
+    assert lib.tnlbm_batch_set_clusters(None, None, 0) == -1
+    assert lib.tnlbm_batch_tune_clusters(None, 1, ms, 17) == -1
+    assert b"tune_clusters" in lib.tnlbm_last_error()
     c = nat.Config()
     c.n_per_axis = 3
     c.lattice = 19
@@ -138,5 +148,10 @@ def test_argument_errors_of_the_precision_and_failure_options(lib):
     c.learned_rank = 2                  # the rank model needs a trained network first
     assert lib.tnlbm_create(ctypes.byref(c), ctypes.byref(h)) == -1
     assert b"learned_rank" in lib.tnlbm_last_error()
+    c.learned_rank = 3                  # batched steps take the full SVD
+    arr = (nat.Config * 2)(c, c)
+    assert lib.tnlbm_batch_create(arr, 2, ctypes.byref(h)) == -1
+    assert b"learned_rank" in lib.tnlbm_last_error() and not h.value
+    c.learned_rank = 0
     # primitives: precision beyond the enum
     assert lib.tnlbm_lincomb_round(9, 3, 1, 1, None, None, None, 8, 8, 0.0, None) == -1
